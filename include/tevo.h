@@ -1,0 +1,185 @@
+/*
+ * tevo.h -- C ABI of the GB300 (sm_103a) library for the higher-order
+ * time-evolution MPO method of Van Damme, Haegeman, McCulloch and
+ * Vanderstraeten, "Efficient higher-order matrix product operators for time
+ * evolution", arXiv:2302.14181.
+ *
+ * The library applies the order-N time-evolution MPO W^(N)(tau) of the paper
+ * to a finite matrix product state and fits the product back into an MPS of
+ * fixed bond dimension by variational sweeps, one time step after another.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Complex numbers cross the ABI as interleaved pairs of doubles (re, im).
+ *    A "complex array of n entries" is a pointer to 2n doubles.
+ *  - Host arrays are owned by the caller and only read (or written) during the
+ *    call; the library keeps no pointer to them.
+ *  - Device memory is owned by the handles (tevo_mpo, tevo_mps) and released by
+ *    their destroy calls. It comes from the allocator registered with
+ *    tevo_ctx_set_allocator, else from cudaMallocAsync on the context stream.
+ *  - Every call is ordered on the context's CUDA stream. Calls that write host
+ *    outputs synchronise that stream before returning.
+ *  - Every entry point returns 0 on success or a negative TEVO_E* code; no
+ *    exception crosses the ABI. tevo_strerror() names a code. After an error the
+ *    handles stay valid but the state they hold is unspecified.
+ *  - A handle is used by one host thread at a time.
+ */
+#ifndef TEVO_H
+#define TEVO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define TEVO_OK 0
+#define TEVO_EINVAL (-1)         /* NULL handle/pointer or argument out of range */
+#define TEVO_ESHAPE (-2)         /* dimensions of the operands do not fit together */
+#define TEVO_ETAU (-3)           /* tau passed to evolve_step differs from the MPO's tau */
+#define TEVO_ENOMEM (-4)         /* device or host allocation failed */
+#define TEVO_ECUDA (-5)          /* a CUDA runtime call or kernel launch failed */
+#define TEVO_ENONFINITE (-6)     /* a NaN or Inf appeared (norm of the fitted state) */
+#define TEVO_ETIMEOUT (-7)       /* a bounded device-side wait gave up */
+#define TEVO_EUNSUPPORTED (-8)   /* precision/shape combination not built */
+
+/* precision of the environment and apply contractions in evolve_step */
+#define TEVO_FP64 0      /* all contractions in fp64 (the plain form) */
+#define TEVO_TF32 1      /* tcgen05 kind::tf32, fp32 accumulate; fp64 QR and final sweep */
+#define TEVO_TF32X3 2    /* three-pass split tf32 (hi*hi + hi*lo + lo*hi); fp64 QR and final sweep */
+#define TEVO_BF16X3 3    /* three-pass split bf16 (hi*hi + hi*lo + lo*hi); fp64 QR and final sweep */
+
+/* variants of the MPO construction (Secs. 3-6 of the paper) */
+#define TEVO_MPO_PLAIN 0     /* Algorithm 1 only (Eq. W1 at N = 1, Eq. W2 at N = 2) */
+#define TEVO_MPO_EXACT 1     /* Algorithms 1 + 2 */
+#define TEVO_MPO_EXTENDED 2  /* Algorithms 3 + 1 + 2 */
+#define TEVO_MPO_FULL 3      /* Algorithms 3 + 1 + 2 + 4: the order-N MPO of the Sec. 7.3 table */
+
+typedef struct tevo_ctx_s* tevo_ctx;
+typedef struct tevo_mpo_s* tevo_mpo;
+typedef struct tevo_mps_s* tevo_mps;
+
+typedef void* (*tevo_alloc_fn)(size_t bytes, void* user);
+typedef void (*tevo_free_fn)(void* ptr, void* user);
+
+/* Create a context bound to a CUDA stream (cudaStream_t passed as void*; NULL is
+ * the legacy default stream) on the current device. */
+int tevo_ctx_create(void* cuda_stream, tevo_ctx* out);
+int tevo_ctx_destroy(tevo_ctx ctx);
+/* Route device allocations of handles created afterwards through alloc/free
+ * (e.g. a framework's caching allocator). alloc must return memory usable on the
+ * context stream, aligned to 256 bytes, or NULL on failure. */
+int tevo_ctx_set_allocator(tevo_ctx ctx, tevo_alloc_fn alloc, tevo_free_fn free_fn, void* user);
+/* Change the stream of an existing context. */
+int tevo_ctx_set_stream(tevo_ctx ctx, void* cuda_stream);
+
+/*
+ * mpo_build -- W^(N)(tau) for a finite chain (Secs. 2.3-6, Algorithms 1-4,
+ * boundary vectors of Eq. boundary), built on the host and uploaded once.
+ *
+ * The Hamiltonian is given per site in the upper-triangular block form of Eq.
+ * jordan_mpo, H = sum_i (D_i + C_i B_{i+1} + C_i A_{i+1} B_{i+2} + ...):
+ *   A  : complex [L][chi][chi][d][d]  (left virtual, right virtual, out, in)
+ *   B  : complex [L][chi][d][d]       (left virtual, out, in)
+ *   C  : complex [L][chi][d][d]       (right virtual, out, in)
+ *   Dh : complex [L][d][d]
+ * Host pointers, row-major, read during the call only.
+ * N in 1..6 is the order, (tau_re, tau_im) the complex step of exp(tau H)
+ * (real time t uses tau = -i dt), variant one of TEVO_MPO_*.
+ * The site tensors are W_i[w_l][s][s'][w_r] with the level (1,...,1) at index 0;
+ * the first site keeps only that row and the last site only that column.
+ * Errors: TEVO_EINVAL (bad pointer, L < 2, d < 1, chi < 1, N out of range),
+ * TEVO_ENOMEM, TEVO_ECUDA.
+ */
+int mpo_build(tevo_ctx ctx, int L, int d, int chi, const double* A, const double* B,
+              const double* C, const double* Dh, int N, double tau_re, double tau_im,
+              int variant, tevo_mpo* out);
+/*
+ * mpo_build_host -- the same construction as mpo_build, on the host only (no
+ * device memory, no CUDA call). Writes the bond dimensions w_0..w_L into w_out
+ * (L+1 ints) and, when W_out is not NULL, the site tensors W_i[w_l][d][d][w_r]
+ * back to back as complex entries into W_out, which must hold *count entries;
+ * *count always receives the total number of complex entries.
+ * Errors: TEVO_EINVAL, TEVO_ENOMEM.
+ */
+int mpo_build_host(int L, int d, int chi, const double* A, const double* B, const double* C,
+                   const double* Dh, int N, double tau_re, double tau_im, int variant, int* w_out,
+                   double* W_out, size_t* count);
+
+/* bond dimensions w_0..w_L of the built MPO (host array of L+1 ints) */
+int mpo_bond_dims(tevo_mpo W, int* w_out);
+/* copy site i's tensor W_i[w_l][d][d][w_r] to host (complex, w_l*d*d*w_r entries) */
+int mpo_get_site(tevo_mpo W, int i, double* host_out);
+int mpo_destroy(tevo_mpo W);
+
+/*
+ * mps_init -- product state |v_1> (x) ... (x) |v_L> held at the bond dimensions
+ * D_i = min(D, d^i, d^(L-i)), the product in index 0 of every bond and zeros
+ * elsewhere (Sec. 2.1 MPS; the padding reading is stated in the design notes).
+ * site_vectors: complex [L][d], host. Errors: TEVO_EINVAL, TEVO_ENOMEM.
+ */
+int mps_init(tevo_ctx ctx, int L, int d, int D, const double* site_vectors, tevo_mps* out);
+/* bond dimensions D_0..D_L (host array of L+1 ints) */
+int mps_bond_dims(tevo_mps psi, int* dims_out);
+/* copy site i's tensor A_i[D_{i-1}][d][D_i] to/from host (complex).
+ * mps_set_site marks the state as not canonical. */
+int mps_get_site(tevo_mps psi, int i, double* host_out);
+int mps_set_site(tevo_mps psi, int i, const double* host_in);
+/* accumulated log of the norm removed by the normalisation of each time step */
+int mps_log_norm(tevo_mps psi, double* out);
+int mps_destroy(tevo_mps psi);
+
+/*
+ * evolve_step -- one time step psi <- W psi / ||W psi||, fitted at psi's bond
+ * dimensions by variational sweeps (Sec. 2.2 and Table 1, "(i)DMRG" row; the
+ * set-up of Sec. 7.2: one variational fit per time step at fixed bond
+ * dimension).
+ *
+ * The step starts from phi = psi (right-canonical), builds the right
+ * environments of <phi|W|psi>, and runs `sweeps` sweeps (sites 1..L-1 moving
+ * right with a Householder QR re-gauge, then sites L..2 moving left as the same
+ * step on the mirrored chain), then recomputes the centre at site 1, normalises
+ * it and accumulates log ||.|| in the state's log-norm.
+ * tau must equal the tau W was built with (TEVO_ETAU otherwise); D must equal
+ * the cap psi was created with (TEVO_ESHAPE otherwise). precision is one of
+ * TEVO_FP64 / TF32 / TF32X3 / BF16X3: for the low-precision forms the first
+ * sweeps-1 sweeps use tensor-core contractions and the last sweep (preceded by
+ * a rebuild of the right environments) is fp64; the QR, the norm and every
+ * reduction are fp64 in all forms.
+ * Errors: TEVO_EINVAL, TEVO_ESHAPE, TEVO_ETAU, TEVO_ENOMEM, TEVO_ECUDA,
+ * TEVO_ENONFINITE (norm of the fitted state is 0, NaN or Inf),
+ * TEVO_EUNSUPPORTED. Asynchronous on the context stream.
+ */
+int evolve_step(tevo_mps psi, tevo_mpo W, double tau_re, double tau_im, int D, int sweeps,
+                int precision);
+
+/*
+ * measure_local -- <O_i> = <psi|O_i|psi>/<psi|psi> for every site i and each of
+ * nops single-site operators (the local observables of Sec. 7.2), in any gauge.
+ * ops: complex [nops][d][d] host; out: complex [nops][L] host.
+ * Errors: TEVO_EINVAL, TEVO_ENOMEM, TEVO_ECUDA. Synchronises the stream.
+ */
+int measure_local(tevo_mps psi, int nops, const double* ops, double* out);
+
+/*
+ * mps_overlap -- <a|b> of the stored (normalised) tensors, returned as
+ * log|<a|b>| and arg <a|b> so that long chains neither overflow nor underflow
+ * (the fidelity density of Eq. fid is log_abs / L). The transfer matrix is
+ * rescaled at every site. a and b need the same L and d.
+ * Errors: TEVO_EINVAL, TEVO_ESHAPE, TEVO_ENOMEM, TEVO_ECUDA. Synchronises.
+ */
+int mps_overlap(tevo_mps a, tevo_mps b, double* log_abs, double* phase);
+
+/* name of an error code */
+const char* tevo_strerror(int code);
+
+/* number of kernels this library launched on the context since creation or the
+ * last reset (host-side count of launches issued by the library) */
+int tevo_launch_count(tevo_ctx ctx, long long* count, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TEVO_H */

@@ -1,0 +1,811 @@
+// C ABI and the host-side sweep driver of libtevo (see include/tevo.h).
+//
+// Data layout in device memory (complex fp64 as interleaved doubles):
+//   MPS site i        A_i[D_i][d][D_{i+1}]          (two sets: psi and the fitted phi)
+//   MPO site i        W_i[wl][d][d][wr]             (plus the G2 operands below)
+//                     Wr_i[(s wr)][(wl s')]          rightward step
+//                     Wl_i[(s wl)][(wr s')]          leftward step (mirrored chain)
+//   environment slot b (bond b = 0..L): [D_b][w_b][D_b]; it holds the left
+//   environment of <phi|W|psi> for bonds left of the sweep position and the
+//   right environment for the others, so one slab of L+1 slots serves both.
+//
+// A site step in the rightward layout (El, A, W, Er) -> (Q, Enew) is
+//   G1  X[(p w), (s' b)]  = El[(p w), a] A[a, (s' b)]
+//   G2  T_p[(s v), b]     = Wr[(s v), (w s')] X_p[(w s'), b]        (batched over p)
+//   G3  B[(p s), q]       = T[(p s), (v b)] Er[q, (v b)]            (column-major out)
+//   QR  B = Q R (Householder, fp64)
+//   G3' Enew[q, (v b)]    = conj(Q)[(p s), q] T[(p s), (v b)]
+// and the leftward step is the same on the mirrored chain: the site tensor is
+// transposed A^T[r][s][l], the environments swap roles and Wl replaces Wr.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tevo_internal.h"
+#include "tevo_mixed.h"
+
+using namespace tevo;
+
+struct tevo_ctx_s {
+  cudaStream_t stream = nullptr;
+  tevo_alloc_fn alloc = nullptr;
+  tevo_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  long long launches = 0;
+  int device = 0;
+  int num_sms = 1;
+};
+
+namespace {
+
+#define TRY(x)                  \
+  do {                          \
+    int _e = (x);               \
+    if (_e) return _e;          \
+  } while (0)
+#define TRYCUDA(x)                                  \
+  do {                                              \
+    if ((x) != cudaSuccess) return TEVO_ECUDA;      \
+  } while (0)
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+int dalloc(tevo_ctx c, Buf& b, size_t bytes) {
+  b.bytes = bytes;
+  b.p = nullptr;
+  if (bytes == 0) return 0;
+  if (c->alloc) {
+    b.p = c->alloc(bytes, c->user);
+  } else {
+    if (cudaMallocAsync(&b.p, bytes, c->stream) != cudaSuccess) b.p = nullptr;
+  }
+  return b.p ? 0 : TEVO_ENOMEM;
+}
+
+void dfree(tevo_ctx c, Buf& b) {
+  if (!b.p) return;
+  if (c->free_fn)
+    c->free_fn(b.p, c->user);
+  else
+    cudaFreeAsync(b.p, c->stream);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+int ensure(tevo_ctx c, Buf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return 0;
+  dfree(c, b);
+  return dalloc(c, b, bytes);
+}
+
+Launch launch_of(tevo_ctx c) { return Launch{c->stream, &c->launches, c->num_sms}; }
+
+inline z64* zp(const Buf& b) { return reinterpret_cast<z64*>(b.p); }
+
+}  // namespace
+
+struct tevo_mpo_s {
+  tevo_ctx ctx = nullptr;
+  int L = 0, d = 0, chi = 0, N = 0, variant = 0;
+  double tau_re = 0, tau_im = 0;
+  std::vector<int> wl, wr;
+  std::vector<Buf> W, Wr, Wl;
+  std::vector<std::vector<std::complex<double>>> host;  // W_i on the host (test access)
+  MixedMPO* mixed = nullptr;                            // low-precision operands (lazy)
+};
+
+struct tevo_mps_s {
+  tevo_ctx ctx = nullptr;
+  int L = 0, d = 0, D = 0;
+  std::vector<int> dims;
+  std::vector<Buf> A, Anew;
+  bool canonical = false;
+  Buf scalars;  // [0] lognorm, [1] nrm2, [2] overlap log acc, [3..] flags/values
+  // workspace of evolve_step
+  std::vector<size_t> env_off;
+  Buf env, X, T, Bq, V, tau, beta, Atmp, Rm, gemm_ws, red;
+  int wmax = 0;
+  MixedState* mixed = nullptr;
+};
+
+namespace {
+
+double* scal(tevo_mps s, int k) { return reinterpret_cast<double*>(s->scalars.p) + k; }
+
+int gemm(tevo_mps s, const GemmDesc& g) {
+  Launch L = launch_of(s->ctx);
+  return zgemm64(L, g, s->gemm_ws.p, s->gemm_ws.bytes);
+}
+
+GemmDesc gd(const void* A, long long sAb, long long sAm, long long sAk, const void* B, long long sBb,
+            long long sBk, long long sBn, void* C, long long sCb, long long sCm, long long sCn, int M,
+            int N, int K, int batch, int conjA = 0) {
+  GemmDesc g;
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.batch = batch;
+  g.sAb = sAb;
+  g.sAm = sAm;
+  g.sAk = sAk;
+  g.sBb = sBb;
+  g.sBk = sBk;
+  g.sBn = sBn;
+  g.sCb = sCb;
+  g.sCm = sCm;
+  g.sCn = sCn;
+  g.conjA = conjA;
+  g.conjB = 0;
+  g.alpha_re = 1;
+  g.alpha_im = 0;
+  g.beta_re = 0;
+  g.beta_im = 0;
+  return g;
+}
+
+z64* env_slot(tevo_mps s, int b) { return reinterpret_cast<z64*>(static_cast<char*>(s->env.p) + s->env_off[b]); }
+
+// sizes of one site step in the rightward layout
+struct StepDims {
+  int Dp, Da, wl, d, Db, Dq, wr;
+};
+
+// G1 + G2: T from (El, A, Wg) in fp64
+int make_T64(tevo_mps s, const StepDims& k, const z64* El, const z64* A, const z64* Wg) {
+  // G1: X[(p w), (s' b)] = El[(p w), a] A[a, (s' b)]
+  TRY(gemm(s, gd(El, 0, k.Da, 1, A, 0, (long long)k.d * k.Db, 1, s->X.p, 0, (long long)k.d * k.Db, 1,
+                 k.Dp * k.wl, k.d * k.Db, k.Da, 1)));
+  // G2: T_p[(s v), b] = Wg[(s v), (w s')] X_p[(w s'), b]
+  TRY(gemm(s, gd(Wg, 0, (long long)k.wl * k.d, 1, s->X.p, (long long)k.wl * k.d * k.Db, k.Db, 1, s->T.p,
+                 (long long)k.d * k.wr * k.Db, k.Db, 1, k.d * k.wr, k.Db, k.wl * k.d, k.Dp)));
+  return 0;
+}
+
+// G3: column-major B = T Er^T
+int apply64(tevo_mps s, const StepDims& k, const z64* Er, z64* Bc) {
+  const int M = k.Dp * k.d;
+  return gemm(s, gd(s->T.p, 0, (long long)k.wr * k.Db, 1, Er, 0, 1, (long long)k.wr * k.Db, Bc, 0, 1, M, M,
+                    k.Dq, k.wr * k.Db, 1));
+}
+
+// G3': Enew[q, (v b)] = sum conj(Q)[(p s), q] T[(p s), (v b)], Q column-major (ld = Dp d)
+int env64(tevo_mps s, const StepDims& k, const z64* Qc, z64* Enew) {
+  const int M = k.Dp * k.d;
+  return gemm(s, gd(Qc, 0, M, 1, s->T.p, 0, (long long)k.wr * k.Db, 1, Enew, 0, (long long)k.wr * k.Db, 1,
+                    k.Dq, k.wr * k.Db, M, 1, /*conjA=*/1));
+}
+
+// QR of the column-major Bq (m x n) and explicit Q written back into Bq
+int qr_q(tevo_mps s, int m, int n, bool keep_r) {
+  Launch L = launch_of(s->ctx);
+  TRY(qr64_factor(L, zp(s->Bq), m, n, zp(s->V), zp(s->tau), zp(s->beta), static_cast<double*>(s->red.p)));
+  if (keep_r) TRY(qr64_extract_r(L, zp(s->Bq), zp(s->beta), m, n, zp(s->Rm)));
+  return qr64_form_q(L, zp(s->V), zp(s->tau), m, n, zp(s->Bq), 1, m);
+}
+
+// store a column-major (Dl d) x Dr matrix as the site tensor [Dl][d][Dr]
+int store_right(tevo_mps s, const z64* Bc, z64* site, int Dl, int d, int Dr) {
+  const int m = Dl * d;
+  return copy2d64(launch_of(s->ctx), Bc, 1, m, site, Dr, 1, m, Dr);
+}
+
+// store a column-major (Dr d) x Dl matrix (mirrored chain) as the site tensor [Dl][d][Dr]
+int store_left(tevo_mps s, const z64* Bc, z64* site, int Dl, int d, int Dr) {
+  const int m = Dr * d;
+  Launch L = launch_of(s->ctx);
+  TRY(copy2d64(L, Bc, 1, m, zp(s->Atmp), Dl, 1, m, Dl));  // -> [Dr][d][Dl]
+  return mirror_site64(L, zp(s->Atmp), site, Dr, d, Dl);
+}
+
+int workspace(tevo_mps s, tevo_mpo W) {
+  tevo_ctx c = s->ctx;
+  const int L = s->L, d = s->d;
+  int wmax = 1;
+  for (int i = 0; i < L; ++i) wmax = std::max({wmax, W->wl[i], W->wr[i]});
+  if (s->env.p && s->wmax >= wmax) return 0;
+  s->wmax = wmax;
+  s->env_off.assign(L + 1, 0);
+  size_t off = 0;
+  for (int b = 0; b <= L; ++b) {
+    s->env_off[b] = off;
+    int wb = (b == 0 || b == L) ? 1 : W->wr[b - 1];
+    size_t bytes = sizeof(z64) * (size_t)s->dims[b] * wb * s->dims[b];
+    off += (bytes + 255) / 256 * 256;
+  }
+  TRY(ensure(c, s->env, off));
+  size_t xt = 0, bq = 0;
+  for (int i = 0; i < L; ++i) {
+    size_t a = (size_t)s->dims[i] * W->wl[i] * d * s->dims[i + 1];
+    size_t b2 = (size_t)s->dims[i + 1] * W->wr[i] * d * s->dims[i];
+    xt = std::max({xt, a, b2});
+    bq = std::max(bq, (size_t)s->dims[i] * d * s->dims[i + 1]);
+  }
+  TRY(ensure(c, s->X, sizeof(z64) * xt));
+  TRY(ensure(c, s->T, sizeof(z64) * xt));
+  TRY(ensure(c, s->Bq, sizeof(z64) * bq));
+  TRY(ensure(c, s->V, sizeof(z64) * bq));
+  TRY(ensure(c, s->Atmp, sizeof(z64) * bq));
+  TRY(ensure(c, s->tau, sizeof(z64) * (size_t)(s->D * d + 8)));
+  TRY(ensure(c, s->beta, sizeof(z64) * (size_t)(s->D * d + 8)));
+  TRY(ensure(c, s->Rm, sizeof(z64) * (size_t)s->D * s->D + 64));
+  TRY(ensure(c, s->gemm_ws, (size_t)48 << 20));
+  TRY(ensure(c, s->red, sizeof(double) * 4096));
+  return 0;
+}
+
+// LQ sweep from site L-1 down to 1 on the mirrored chain (Householder QR of
+// the transposed site, R^T absorbed into the left neighbour)
+int right_canonicalize(tevo_mps s, std::vector<Buf>& t) {
+  Launch L = launch_of(s->ctx);
+  const int d = s->d;
+  for (int i = s->L - 1; i >= 1; --i) {
+    const int Dl = s->dims[i], Dr = s->dims[i + 1];
+    const int m = Dr * d, n = Dl;
+    // mirrored site as a column-major m x n matrix: element ((r s), l) = A[l][s][r]
+    TRY(mirror_site64(L, zp(t[i]), zp(s->Atmp), Dl, d, Dr));          // [Dr][d][Dl] = row-major m x n
+    TRY(copy2d64(L, zp(s->Atmp), n, 1, zp(s->Bq), 1, m, m, n));       // -> column-major
+    TRY(qr_q(s, m, n, true));
+    TRY(store_left(s, zp(s->Bq), zp(t[i]), Dl, d, Dr));
+    // left neighbour: A'[a][s][k] = sum_l A[a][s][l] R[k][l]
+    const int Dll = s->dims[i - 1];
+    TRY(gemm(s, gd(t[i - 1].p, 0, Dl, 1, s->Rm.p, 0, 1, n, s->Atmp.p, 0, n, 1, Dll * d, n, Dl, 1)));
+    TRY(copy2d64(L, zp(s->Atmp), n, 1, zp(t[i - 1]), n, 1, Dll * d, n));
+  }
+  return 0;
+}
+
+StepDims right_dims(tevo_mps s, tevo_mpo W, int i) {
+  return StepDims{s->dims[i], s->dims[i], W->wl[i], s->d, s->dims[i + 1], s->dims[i + 1], W->wr[i]};
+}
+StepDims left_dims(tevo_mps s, tevo_mpo W, int i) {
+  return StepDims{s->dims[i + 1], s->dims[i + 1], W->wr[i], s->d, s->dims[i], s->dims[i], W->wl[i]};
+}
+
+// one fp64 sweep (rightward over 0..L-2, then leftward over L-1..1)
+int sweep64(tevo_mps s, tevo_mpo W) {
+  Launch L = launch_of(s->ctx);
+  const int d = s->d;
+  for (int i = 0; i + 1 < s->L; ++i) {
+    StepDims k = right_dims(s, W, i);
+    TRY(make_T64(s, k, env_slot(s, i), zp(s->A[i]), zp(W->Wr[i])));
+    TRY(apply64(s, k, env_slot(s, i + 1), zp(s->Bq)));
+    TRY(qr_q(s, k.Dp * d, k.Dq, false));
+    TRY(store_right(s, zp(s->Bq), zp(s->Anew[i]), k.Dp, d, k.Dq));
+    TRY(env64(s, k, zp(s->Bq), env_slot(s, i + 1)));
+  }
+  for (int i = s->L - 1; i >= 1; --i) {
+    StepDims k = left_dims(s, W, i);
+    TRY(mirror_site64(L, zp(s->A[i]), zp(s->Atmp), s->dims[i], d, s->dims[i + 1]));
+    TRY(make_T64(s, k, env_slot(s, i + 1), zp(s->Atmp), zp(W->Wl[i])));
+    TRY(apply64(s, k, env_slot(s, i), zp(s->Bq)));
+    TRY(qr_q(s, k.Dp * d, k.Dq, false));
+    TRY(store_left(s, zp(s->Bq), zp(s->Anew[i]), k.Dq, d, k.Dp));
+    TRY(env64(s, k, zp(s->Bq), env_slot(s, i)));
+  }
+  return 0;
+}
+
+// right environments of <bra|W|ket> for bonds L-1..1 (slot L holds 1)
+int build_right_envs64(tevo_mps s, tevo_mpo W, std::vector<Buf>& bra, std::vector<Buf>& ket) {
+  Launch L = launch_of(s->ctx);
+  const int d = s->d;
+  for (int i = s->L - 1; i >= 1; --i) {
+    StepDims k = left_dims(s, W, i);
+    TRY(mirror_site64(L, zp(ket[i]), zp(s->Atmp), s->dims[i], d, s->dims[i + 1]));
+    TRY(make_T64(s, k, env_slot(s, i + 1), zp(s->Atmp), zp(W->Wl[i])));
+    // bra^T as a column-major (Dr d) x Dl matrix
+    TRY(mirror_site64(L, zp(bra[i]), zp(s->Atmp), s->dims[i], d, s->dims[i + 1]));
+    TRY(copy2d64(L, zp(s->Atmp), k.Dq, 1, zp(s->Bq), 1, k.Dp * d, k.Dp * d, k.Dq));
+    TRY(env64(s, k, zp(s->Bq), env_slot(s, i)));
+  }
+  return 0;
+}
+
+int centre64(tevo_mps s, tevo_mpo W) {
+  Launch L = launch_of(s->ctx);
+  const int d = s->d;
+  StepDims k = left_dims(s, W, 0);
+  TRY(mirror_site64(L, zp(s->A[0]), zp(s->Atmp), s->dims[0], d, s->dims[1]));
+  TRY(make_T64(s, k, env_slot(s, 1), zp(s->Atmp), zp(W->Wl[0])));
+  TRY(apply64(s, k, env_slot(s, 0), zp(s->Bq)));
+  TRY(store_left(s, zp(s->Bq), zp(s->Anew[0]), k.Dq, d, k.Dp));
+  return 0;
+}
+
+int finish_step(tevo_mps s) {
+  Launch L = launch_of(s->ctx);
+  const size_t n0 = (size_t)s->dims[0] * s->d * s->dims[1];
+  TRY(norm2_64(L, zp(s->Anew[0]), n0, scal(s, 1), static_cast<double*>(s->red.p)));
+  TRY(normalize64(L, zp(s->Anew[0]), n0, scal(s, 1), scal(s, 0), reinterpret_cast<int*>(scal(s, 4))));
+  std::swap(s->A, s->Anew);
+  s->canonical = true;
+  return 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" int tevo_ctx_create(void* stream, tevo_ctx* out) {
+  if (!out) return TEVO_EINVAL;
+  tevo_ctx c = new (std::nothrow) tevo_ctx_s;
+  if (!c) return TEVO_ENOMEM;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return TEVO_ECUDA;
+  }
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return TEVO_ECUDA;
+  }
+  *out = c;
+  return 0;
+}
+
+extern "C" int tevo_ctx_destroy(tevo_ctx c) {
+  if (!c) return TEVO_EINVAL;
+  delete c;
+  return 0;
+}
+
+extern "C" int tevo_ctx_set_allocator(tevo_ctx c, tevo_alloc_fn a, tevo_free_fn f, void* user) {
+  if (!c || (a == nullptr) != (f == nullptr)) return TEVO_EINVAL;
+  c->alloc = a;
+  c->free_fn = f;
+  c->user = user;
+  return 0;
+}
+
+extern "C" int tevo_ctx_set_stream(tevo_ctx c, void* stream) {
+  if (!c) return TEVO_EINVAL;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  return 0;
+}
+
+extern "C" int tevo_launch_count(tevo_ctx c, long long* count, int reset) {
+  if (!c || !count) return TEVO_EINVAL;
+  *count = c->launches;
+  if (reset) c->launches = 0;
+  return 0;
+}
+
+extern "C" const char* tevo_strerror(int code) {
+  switch (code) {
+    case TEVO_OK: return "ok";
+    case TEVO_EINVAL: return "invalid argument";
+    case TEVO_ESHAPE: return "shape mismatch";
+    case TEVO_ETAU: return "tau differs from the MPO's tau";
+    case TEVO_ENOMEM: return "out of memory";
+    case TEVO_ECUDA: return "CUDA error";
+    case TEVO_ENONFINITE: return "non-finite norm";
+    case TEVO_ETIMEOUT: return "device wait timed out";
+    case TEVO_EUNSUPPORTED: return "unsupported";
+    default: return "unknown error";
+  }
+}
+
+// ---------------------------------------------------------------------------
+// MPO
+// ---------------------------------------------------------------------------
+extern "C" int mpo_build(tevo_ctx c, int L, int d, int chi, const double* A, const double* B, const double* C,
+                         const double* Dh, int N, double tau_re, double tau_im, int variant, tevo_mpo* out) {
+  if (!c || !A || !B || !C || !Dh || !out) return TEVO_EINVAL;
+  if (L < 2 || d < 1 || chi < 1 || N < 1 || N > 6 || variant < 0 || variant > 3) return TEVO_EINVAL;
+  if (!std::isfinite(tau_re) || !std::isfinite(tau_im)) return TEVO_EINVAL;
+  tevo_mpo W = new (std::nothrow) tevo_mpo_s;
+  if (!W) return TEVO_ENOMEM;
+  W->ctx = c;
+  W->L = L;
+  W->d = d;
+  W->chi = chi;
+  W->N = N;
+  W->variant = variant;
+  W->tau_re = tau_re;
+  W->tau_im = tau_im;
+  try {
+    build_mpo_host(L, d, chi, A, B, C, Dh, N, tau_re, tau_im, variant, W->host, W->wl, W->wr);
+  } catch (...) {
+    delete W;
+    return TEVO_ENOMEM;
+  }
+  W->W.resize(L);
+  W->Wr.resize(L);
+  W->Wl.resize(L);
+  for (int i = 0; i < L; ++i) {
+    const int wl = W->wl[i], wr = W->wr[i];
+    const auto& S = W->host[i];
+    std::vector<std::complex<double>> gr((size_t)d * wr * wl * d), gl((size_t)d * wl * wr * d);
+    for (int a = 0; a < wl; ++a)
+      for (int s = 0; s < d; ++s)
+        for (int t = 0; t < d; ++t)
+          for (int b = 0; b < wr; ++b) {
+            auto v = S[((size_t(a) * d + s) * d + t) * wr + b];
+            gr[((size_t)s * wr + b) * (wl * d) + (size_t)a * d + t] = v;  // [(s wr)][(wl s')]
+            gl[((size_t)s * wl + a) * (wr * d) + (size_t)b * d + t] = v;  // [(s wl)][(wr s')]
+          }
+    const size_t bytes = sizeof(z64) * S.size();
+    int e = dalloc(c, W->W[i], bytes);
+    if (!e) e = dalloc(c, W->Wr[i], bytes);
+    if (!e) e = dalloc(c, W->Wl[i], bytes);
+    if (e) {
+      mpo_destroy(W);
+      return e;
+    }
+    if (cudaMemcpyAsync(W->W[i].p, S.data(), bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(W->Wr[i].p, gr.data(), bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(W->Wl[i].p, gl.data(), bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      mpo_destroy(W);
+      return TEVO_ECUDA;
+    }
+  }
+  *out = W;
+  return 0;
+}
+
+extern "C" int mpo_build_host(int L, int d, int chi, const double* A, const double* B, const double* C,
+                              const double* Dh, int N, double tau_re, double tau_im, int variant, int* w_out,
+                              double* W_out, size_t* count) {
+  if (!A || !B || !C || !Dh || !w_out || !count) return TEVO_EINVAL;
+  if (L < 2 || d < 1 || chi < 1 || N < 1 || N > 6 || variant < 0 || variant > 3) return TEVO_EINVAL;
+  std::vector<std::vector<std::complex<double>>> sites;
+  std::vector<int> wl, wr;
+  try {
+    build_mpo_host(L, d, chi, A, B, C, Dh, N, tau_re, tau_im, variant, sites, wl, wr);
+  } catch (...) {
+    return TEVO_ENOMEM;
+  }
+  size_t total = 0;
+  for (auto& v : sites) total += v.size();
+  w_out[0] = wl[0];
+  for (int i = 0; i < L; ++i) w_out[i + 1] = wr[i];
+  if (W_out) {
+    if (*count < total) return TEVO_EINVAL;
+    size_t off = 0;
+    for (auto& v : sites) {
+      std::memcpy(W_out + 2 * off, v.data(), sizeof(z64) * v.size());
+      off += v.size();
+    }
+  }
+  *count = total;
+  return 0;
+}
+
+extern "C" int mpo_bond_dims(tevo_mpo W, int* w) {
+  if (!W || !w) return TEVO_EINVAL;
+  w[0] = W->wl[0];
+  for (int i = 0; i < W->L; ++i) w[i + 1] = W->wr[i];
+  return 0;
+}
+
+extern "C" int mpo_get_site(tevo_mpo W, int i, double* out) {
+  if (!W || !out || i < 0 || i >= W->L) return TEVO_EINVAL;
+  std::memcpy(out, W->host[i].data(), sizeof(z64) * W->host[i].size());
+  return 0;
+}
+
+extern "C" int mpo_destroy(tevo_mpo W) {
+  if (!W) return TEVO_EINVAL;
+  for (auto& b : W->W) dfree(W->ctx, b);
+  for (auto& b : W->Wr) dfree(W->ctx, b);
+  for (auto& b : W->Wl) dfree(W->ctx, b);
+  mixed_mpo_destroy(W->ctx, W->mixed);
+  delete W;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// MPS
+// ---------------------------------------------------------------------------
+extern "C" int mps_init(tevo_ctx c, int L, int d, int D, const double* v, tevo_mps* out) {
+  if (!c || !v || !out || L < 2 || d < 1 || D < 1) return TEVO_EINVAL;
+  tevo_mps s = new (std::nothrow) tevo_mps_s;
+  if (!s) return TEVO_ENOMEM;
+  s->ctx = c;
+  s->L = L;
+  s->d = d;
+  s->D = D;
+  s->dims.resize(L + 1);
+  for (int i = 0; i <= L; ++i) {
+    long long p = 1;
+    for (int k = 0; k < std::min(i, L - i) && p < D; ++k) p = std::min<long long>(p * d, D);
+    s->dims[i] = int(p);
+  }
+  s->A.resize(L);
+  s->Anew.resize(L);
+  int e = dalloc(c, s->scalars, sizeof(double) * 16);
+  for (int i = 0; i < L && !e; ++i) {
+    const size_t n = (size_t)s->dims[i] * d * s->dims[i + 1];
+    e = dalloc(c, s->A[i], sizeof(z64) * n);
+    if (!e) e = dalloc(c, s->Anew[i], sizeof(z64) * n);
+    if (!e) {
+      std::vector<z64> h(n, z64{0, 0});
+      for (int t = 0; t < d; ++t) h[(size_t)t * s->dims[i + 1]] = z64{v[2 * ((size_t)i * d + t)], v[2 * ((size_t)i * d + t) + 1]};
+      if (cudaMemcpyAsync(s->A[i].p, h.data(), sizeof(z64) * n, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess)
+        e = TEVO_ECUDA;
+    }
+  }
+  if (!e) {
+    double z[16] = {0};
+    if (cudaMemcpyAsync(s->scalars.p, z, sizeof(z), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      e = TEVO_ECUDA;
+  }
+  if (e) {
+    mps_destroy(s);
+    return e;
+  }
+  *out = s;
+  return 0;
+}
+
+extern "C" int mps_bond_dims(tevo_mps s, int* out) {
+  if (!s || !out) return TEVO_EINVAL;
+  for (int i = 0; i <= s->L; ++i) out[i] = s->dims[i];
+  return 0;
+}
+
+extern "C" int mps_get_site(tevo_mps s, int i, double* out) {
+  if (!s || !out || i < 0 || i >= s->L) return TEVO_EINVAL;
+  const size_t n = (size_t)s->dims[i] * s->d * s->dims[i + 1];
+  if (cudaMemcpyAsync(out, s->A[i].p, sizeof(z64) * n, cudaMemcpyDeviceToHost, s->ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->ctx->stream) != cudaSuccess)
+    return TEVO_ECUDA;
+  return 0;
+}
+
+extern "C" int mps_set_site(tevo_mps s, int i, const double* in) {
+  if (!s || !in || i < 0 || i >= s->L) return TEVO_EINVAL;
+  const size_t n = (size_t)s->dims[i] * s->d * s->dims[i + 1];
+  if (cudaMemcpyAsync(s->A[i].p, in, sizeof(z64) * n, cudaMemcpyHostToDevice, s->ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->ctx->stream) != cudaSuccess)
+    return TEVO_ECUDA;
+  s->canonical = false;
+  return 0;
+}
+
+extern "C" int mps_log_norm(tevo_mps s, double* out) {
+  if (!s || !out) return TEVO_EINVAL;
+  if (cudaMemcpyAsync(out, scal(s, 0), sizeof(double), cudaMemcpyDeviceToHost, s->ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->ctx->stream) != cudaSuccess)
+    return TEVO_ECUDA;
+  return 0;
+}
+
+extern "C" int mps_destroy(tevo_mps s) {
+  if (!s) return TEVO_EINVAL;
+  tevo_ctx c = s->ctx;
+  for (auto& b : s->A) dfree(c, b);
+  for (auto& b : s->Anew) dfree(c, b);
+  for (Buf* b : {&s->scalars, &s->env, &s->X, &s->T, &s->Bq, &s->V, &s->tau, &s->beta, &s->Atmp, &s->Rm,
+                 &s->gemm_ws, &s->red})
+    dfree(c, *b);
+  mixed_state_destroy(c, s->mixed);
+  delete s;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// evolve_step
+// ---------------------------------------------------------------------------
+extern "C" int evolve_step(tevo_mps s, tevo_mpo W, double tau_re, double tau_im, int D, int sweeps, int precision) {
+  if (!s || !W || sweeps < 1) return TEVO_EINVAL;
+  if (precision < TEVO_FP64 || precision > TEVO_BF16X3) return TEVO_EINVAL;
+  if (W->L != s->L || W->d != s->d) return TEVO_ESHAPE;
+  if (D != s->D) return TEVO_ESHAPE;
+  if (tau_re != W->tau_re || tau_im != W->tau_im) return TEVO_ETAU;
+  tevo_ctx c = s->ctx;
+  TRY(workspace(s, W));
+  Launch L = launch_of(c);
+  const int d = s->d;
+  TRY(fill64(L, env_slot(s, 0), 1, 1.0, 0.0));
+  TRY(fill64(L, env_slot(s, s->L), 1, 1.0, 0.0));
+  // bra of the first environments: phi0 = psi, made right-canonical when psi is not
+  std::vector<Buf>* bra = &s->A;
+  if (!s->canonical) {
+    for (int i = 0; i < s->L; ++i) {
+      const size_t n = (size_t)s->dims[i] * d * s->dims[i + 1];
+      TRYCUDA(cudaMemcpyAsync(s->Anew[i].p, s->A[i].p, sizeof(z64) * n, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    TRY(right_canonicalize(s, s->Anew));
+    bra = &s->Anew;
+  }
+  const bool mixed = precision != TEVO_FP64 && sweeps > 1;
+  if (mixed) {
+    TRY(mixed_prepare(c, W, s, precision));
+    TRY(mixed_build_right_envs(c, W, s, bra == &s->Anew, precision));
+    for (int k = 0; k < sweeps - 1; ++k) TRY(mixed_sweep(c, W, s, precision));
+    // fp64 rebuild of the right environments from the fitted phi, then one fp64 sweep
+    TRY(build_right_envs64(s, W, s->Anew, s->A));
+  } else {
+    TRY(build_right_envs64(s, W, *bra, s->A));
+  }
+  const int n64 = mixed ? 1 : sweeps;
+  for (int k = 0; k < n64; ++k) TRY(sweep64(s, W));
+  TRY(centre64(s, W));
+  TRY(finish_step(s));
+  int flag = 0;
+  TRYCUDA(cudaMemcpyAsync(&flag, scal(s, 4), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  TRYCUDA(cudaStreamSynchronize(c->stream));
+  if (flag) return TEVO_ENONFINITE;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+// accessors used by the mixed-precision translation unit
+namespace tevo {
+int mps_L(tevo_mps s) { return s->L; }
+int mps_d(tevo_mps s) { return s->d; }
+const std::vector<int>& mps_dims(tevo_mps s) { return s->dims; }
+MixedState*& mps_mixed(tevo_mps s) { return s->mixed; }
+MixedMPO*& mpo_mixed(tevo_mpo W) { return W->mixed; }
+int mpo_wl(tevo_mpo W, int i) { return W->wl[i]; }
+int mpo_wr(tevo_mpo W, int i) { return W->wr[i]; }
+const void* mpo_dev_wr(tevo_mpo W, int i) { return W->Wr[i].p; }
+const void* mpo_dev_wl(tevo_mpo W, int i) { return W->Wl[i].p; }
+void* mps_site(tevo_mps s, int i, bool fresh) { return fresh ? s->Anew[i].p : s->A[i].p; }
+void* mps_env_slot(tevo_mps s, int b) { return env_slot(s, b); }
+void* mps_buf_T(tevo_mps s) { return s->T.p; }
+void* mps_buf_X(tevo_mps s) { return s->X.p; }
+void* mps_buf_Bq(tevo_mps s) { return s->Bq.p; }
+void* mps_buf_Atmp(tevo_mps s) { return s->Atmp.p; }
+int mps_qr_q(tevo_mps s, int m, int n) { return qr_q(s, m, n, false); }
+int mps_store_right(tevo_mps s, int i) {
+  return store_right(s, zp(s->Bq), zp(s->Anew[i]), s->dims[i], s->d, s->dims[i + 1]);
+}
+int mps_store_left(tevo_mps s, int i) {
+  return store_left(s, zp(s->Bq), zp(s->Anew[i]), s->dims[i], s->d, s->dims[i + 1]);
+}
+int ctx_alloc(tevo_ctx c, void** p, size_t bytes) {
+  Buf b;
+  int e = dalloc(c, b, bytes);
+  *p = b.p;
+  return e;
+}
+void ctx_free(tevo_ctx c, void* p) {
+  Buf b;
+  b.p = p;
+  b.bytes = 1;
+  dfree(c, b);
+}
+Launch ctx_launch(tevo_ctx c) { return launch_of(c); }
+}  // namespace tevo
+
+// ---------------------------------------------------------------------------
+// observables
+// ---------------------------------------------------------------------------
+extern "C" int measure_local(tevo_mps s, int nops, const double* ops, double* out) {
+  if (!s || !ops || !out || nops < 1) return TEVO_EINVAL;
+  tevo_ctx c = s->ctx;
+  Launch Lc = launch_of(c);
+  const int L = s->L, d = s->d;
+  // transfer matrices: El[i] (bond i) from the left, Er[i] from the right, each [D_i][D_i]
+  std::vector<size_t> off(L + 1);
+  size_t tot = 0;
+  for (int b = 0; b <= L; ++b) {
+    off[b] = tot;
+    tot += (size_t)s->dims[b] * s->dims[b];
+  }
+  size_t bq = 0;
+  for (int i = 0; i < L; ++i) bq = std::max(bq, (size_t)s->dims[i] * d * s->dims[i + 1]);
+  Buf El, Er, Y, Z, Wm, OA, opsd, vals;
+  int e = dalloc(c, El, sizeof(z64) * tot);
+  if (!e) e = dalloc(c, Er, sizeof(z64) * tot);
+  if (!e) e = dalloc(c, Y, sizeof(z64) * bq);
+  if (!e) e = dalloc(c, Z, sizeof(z64) * bq);
+  if (!e) e = dalloc(c, OA, sizeof(z64) * bq);
+  if (!e) e = dalloc(c, Wm, sizeof(z64) * (size_t)s->D * s->D + 16);
+  if (!e) e = dalloc(c, opsd, sizeof(z64) * (size_t)nops * d * d);
+  if (!e) e = dalloc(c, vals, sizeof(z64) * ((size_t)nops * L + 1));
+  if (!e) e = ensure(c, s->gemm_ws, (size_t)48 << 20);
+  if (!e) e = ensure(c, s->red, sizeof(double) * 4096);
+  if (!e) e = ensure(c, s->Atmp, sizeof(z64) * bq);
+  auto cleanup = [&]() {
+    for (Buf* b : {&El, &Er, &Y, &Z, &Wm, &OA, &opsd, &vals}) dfree(c, *b);
+  };
+  auto run = [&]() -> int {
+    TRYCUDA(cudaMemcpyAsync(opsd.p, ops, sizeof(z64) * (size_t)nops * d * d, cudaMemcpyHostToDevice, c->stream));
+    z64* el = zp(El);
+    z64* er = zp(Er);
+    TRY(fill64(Lc, el + off[0], 1, 1.0, 0.0));
+    TRY(fill64(Lc, er + off[L], 1, 1.0, 0.0));
+    // El[i+1][a][b] = sum conj(A[a0][s][a]) El[i][a0][b0] A[b0][s][b]
+    for (int i = 0; i < L; ++i) {
+      const int Dl = s->dims[i], Dr = s->dims[i + 1];
+      TRY(gemm(s, gd(el + off[i], 0, Dl, 1, s->A[i].p, 0, (long long)d * Dr, 1, Y.p, 0, (long long)d * Dr, 1, Dl,
+                     d * Dr, Dl, 1)));
+      TRY(gemm(s, gd(s->A[i].p, 0, 1, Dr, Y.p, 0, Dr, 1, el + off[i + 1], 0, Dr, 1, Dr, Dr, Dl * d, 1, 1)));
+    }
+    for (int i = L - 1; i >= 0; --i) {
+      const int Dl = s->dims[i], Dr = s->dims[i + 1];
+      TRY(mirror_site64(Lc, zp(s->A[i]), zp(s->Atmp), Dl, d, Dr));
+      TRY(gemm(s, gd(er + off[i + 1], 0, Dr, 1, s->Atmp.p, 0, (long long)d * Dl, 1, Y.p, 0, (long long)d * Dl, 1,
+                     Dr, d * Dl, Dr, 1)));
+      TRY(gemm(s, gd(s->Atmp.p, 0, 1, Dl, Y.p, 0, Dl, 1, er + off[i], 0, Dl, 1, Dl, Dl, Dr * d, 1, 1)));
+    }
+    for (int i = 0; i < L; ++i) {
+      const int Dl = s->dims[i], Dr = s->dims[i + 1];
+      for (int k = 0; k < nops; ++k) {
+        // OA[a][s][b] = sum_t O[s][t] A[a][t][b]   (batched over a)
+        TRY(gemm(s, gd(zp(opsd) + (size_t)k * d * d, 0, d, 1, s->A[i].p, (long long)d * Dr, Dr, 1, OA.p,
+                       (long long)d * Dr, Dr, 1, d, Dr, d, Dl)));
+        // Z[a][(s b)] = El[i][a][a0] OA[a0][(s b)]
+        TRY(gemm(s, gd(el + off[i], 0, Dl, 1, OA.p, 0, (long long)d * Dr, 1, Z.p, 0, (long long)d * Dr, 1, Dl,
+                       d * Dr, Dl, 1)));
+        // Wm[b][b'] = sum conj(A[(a s)][b]) Z[(a s)][b']
+        TRY(gemm(s, gd(s->A[i].p, 0, 1, Dr, Z.p, 0, Dr, 1, Wm.p, 0, Dr, 1, Dr, Dr, Dl * d, 1, 1)));
+        TRY(dotu64(Lc, zp(Wm), er + off[i + 1], (size_t)Dr * Dr, zp(vals) + (size_t)k * L + i, static_cast<double*>(s->red.p)));
+      }
+    }
+    std::vector<z64> h((size_t)nops * L), nrm(1);
+    TRYCUDA(cudaMemcpyAsync(h.data(), vals.p, sizeof(z64) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+    TRYCUDA(cudaMemcpyAsync(nrm.data(), el + off[L], sizeof(z64), cudaMemcpyDeviceToHost, c->stream));
+    TRYCUDA(cudaStreamSynchronize(c->stream));
+    const double n = nrm[0].x;
+    for (size_t j = 0; j < h.size(); ++j) {
+      out[2 * j] = h[j].x / n;
+      out[2 * j + 1] = h[j].y / n;
+    }
+    return 0;
+  };
+  if (!e) e = run();
+  cleanup();
+  return e;
+}
+
+extern "C" int mps_overlap(tevo_mps a, tevo_mps b, double* log_abs, double* phase) {
+  if (!a || !b || !log_abs || !phase) return TEVO_EINVAL;
+  if (a->L != b->L || a->d != b->d) return TEVO_ESHAPE;
+  tevo_ctx c = b->ctx;
+  Launch Lc = launch_of(c);
+  const int L = a->L, d = a->d;
+  size_t emax = 1, ymax = 1;
+  for (int i = 0; i <= L; ++i) emax = std::max(emax, (size_t)a->dims[i] * b->dims[i]);
+  for (int i = 0; i < L; ++i) ymax = std::max(ymax, (size_t)a->dims[i] * d * b->dims[i + 1]);
+  Buf E0, E1, Y, acc;
+  int e = dalloc(c, E0, sizeof(z64) * emax);
+  if (!e) e = dalloc(c, E1, sizeof(z64) * emax);
+  if (!e) e = dalloc(c, Y, sizeof(z64) * ymax);
+  if (!e) e = dalloc(c, acc, sizeof(double) * 4);
+  if (!e) e = ensure(c, b->gemm_ws, (size_t)48 << 20);
+  if (!e) e = ensure(c, b->red, sizeof(double) * 4096);
+  auto run = [&]() -> int {
+    double zero[4] = {0, 0, 0, 0};
+    TRYCUDA(cudaMemcpyAsync(acc.p, zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream));
+    TRY(fill64(Lc, zp(E0), 1, 1.0, 0.0));
+    for (int i = 0; i < L; ++i) {
+      const int al = a->dims[i], ar = a->dims[i + 1], bl = b->dims[i], br = b->dims[i + 1];
+      // Y[a0][(s b)] = E[a0][b0] B[b0][(s b)];  E'[a][b] = sum conj(A[(a0 s)][a]) Y[(a0 s)][b]
+      TRY(gemm(b, gd(E0.p, 0, bl, 1, b->A[i].p, 0, (long long)d * br, 1, Y.p, 0, (long long)d * br, 1, al, d * br,
+                     bl, 1)));
+      TRY(gemm(b, gd(a->A[i].p, 0, 1, ar, Y.p, 0, br, 1, E1.p, 0, br, 1, ar, br, al * d, 1, 1)));
+      TRY(rescale64(Lc, zp(E1), (size_t)ar * br, reinterpret_cast<double*>(acc.p), static_cast<double*>(b->red.p)));
+      std::swap(E0, E1);
+    }
+    double h[4];
+    z64 z;
+    TRYCUDA(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    TRYCUDA(cudaMemcpyAsync(&z, E0.p, sizeof(z64), cudaMemcpyDeviceToHost, c->stream));
+    TRYCUDA(cudaStreamSynchronize(c->stream));
+    const double az = std::hypot(z.x, z.y);
+    *log_abs = az > 0 ? h[0] + std::log(az) : -INFINITY;
+    *phase = std::atan2(z.y, z.x);
+    return 0;
+  };
+  if (!e) e = run();
+  for (Buf* p : {&E0, &E1, &Y, &acc}) dfree(c, *p);
+  return e;
+}

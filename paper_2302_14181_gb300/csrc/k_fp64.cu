@@ -1,0 +1,580 @@
+// fp64 kernels: strided batched complex GEMM with deterministic split-K,
+// Householder QR (LAPACK reflector convention, deflation of columns with no
+// remaining norm), and the reductions of the fit (norm, rescaling, dot).
+//
+// GB300 executes fp64 at about 2 DFMA per clock per SM, so every kernel here is
+// bound by the fp64 pipe, not by memory: the GEMM keeps one 64x64 complex tile
+// per CTA in registers and splits K until every SM has work.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "tevo_internal.h"
+
+namespace tevo {
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+constexpr int BM = 64, BN = 64, BK = 16, GEMM_THREADS = 256;
+
+struct GemmKArgs {
+  GemmDesc g;
+  int splitK;
+  int kchunk;
+  double2* partial;  // [splitK][batch][M][N] when splitK > 1
+};
+
+template <bool CA, bool CB>
+__global__ void __launch_bounds__(GEMM_THREADS) zgemm_kernel(GemmKArgs p) {
+  __shared__ double2 As[BK][BM];
+  __shared__ double2 Bs[BK][BN];
+  const GemmDesc& g = p.g;
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int bz = blockIdx.z;
+  const int b = bz / p.splitK, sk = bz % p.splitK;
+  const int kbeg = sk * p.kchunk;
+  const int kend = min(g.K, kbeg + p.kchunk);
+  const double2* A = reinterpret_cast<const double2*>(g.A) + (long long)b * g.sAb;
+  const double2* B = reinterpret_cast<const double2*>(g.B) + (long long)b * g.sBb;
+  const bool a_kfast = (g.sAk == 1);
+  const bool b_nfast = (g.sBn == 1);
+  double2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < (BM * BK) / GEMM_THREADS; ++r) {
+      int idx = tid + r * GEMM_THREADS;
+      int mm, kk;
+      if (a_kfast) {
+        mm = idx / BK;
+        kk = idx % BK;
+      } else {
+        mm = idx % BM;
+        kk = idx / BM;
+      }
+      int gm = m0 + mm, gk = k0 + kk;
+      double2 v = make_double2(0.0, 0.0);
+      if (gm < g.M && gk < kend) v = A[(long long)gm * g.sAm + (long long)gk * g.sAk];
+      As[kk][mm] = CA ? cconj(v) : v;
+    }
+#pragma unroll
+    for (int r = 0; r < (BN * BK) / GEMM_THREADS; ++r) {
+      int idx = tid + r * GEMM_THREADS;
+      int nn, kk;
+      if (b_nfast) {
+        nn = idx % BN;
+        kk = idx / BN;
+      } else {
+        nn = idx / BK;
+        kk = idx % BK;
+      }
+      int gn = n0 + nn, gk = k0 + kk;
+      double2 v = make_double2(0.0, 0.0);
+      if (gn < g.N && gk < kend) v = B[(long long)gk * g.sBk + (long long)gn * g.sBn];
+      Bs[kk][nn] = CB ? cconj(v) : v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double2 a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cfma(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+  if (p.splitK > 1) {
+    double2* P = p.partial + ((long long)sk * g.batch + b) * (long long)g.M * g.N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+        if (gm < g.M && gn < g.N) P[(long long)gm * g.N + gn] = acc[i][j];
+      }
+    return;
+  }
+  double2* C = reinterpret_cast<double2*>(g.C) + (long long)b * g.sCb;
+  const double2 alpha = make_double2(g.alpha_re, g.alpha_im);
+  const double2 beta = make_double2(g.beta_re, g.beta_im);
+  const bool use_beta = (g.beta_re != 0.0 || g.beta_im != 0.0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+      if (gm < g.M && gn < g.N) {
+        long long off = (long long)gm * g.sCm + (long long)gn * g.sCn;
+        double2 v = cmul(alpha, acc[i][j]);
+        if (use_beta) v = cfma(beta, C[off], v);
+        C[off] = v;
+      }
+    }
+}
+
+// sum the split-K partials in split order (deterministic) and write C
+__global__ void zgemm_reduce_kernel(GemmDesc g, int splitK, const double2* partial) {
+  const long long MN = (long long)g.M * g.N;
+  const long long total = MN * g.batch;
+  const double2 alpha = make_double2(g.alpha_re, g.alpha_im);
+  const double2 beta = make_double2(g.beta_re, g.beta_im);
+  const bool use_beta = (g.beta_re != 0.0 || g.beta_im != 0.0);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long b = idx / MN, r = idx % MN;
+    int m = int(r / g.N), n = int(r % g.N);
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < splitK; ++k) {
+      double2 v = partial[((long long)k * g.batch + b) * MN + r];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    double2* C = reinterpret_cast<double2*>(g.C) + b * g.sCb;
+    long long off = (long long)m * g.sCm + (long long)n * g.sCn;
+    double2 v = cmul(alpha, s);
+    if (use_beta) v = cfma(beta, C[off], v);
+    C[off] = v;
+  }
+}
+
+void choose_split(const GemmDesc& g, int num_sms, int& splitK, int& kchunk) {
+  long long tiles = (long long)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * g.batch;
+  splitK = 1;
+  long long target = 2LL * num_sms;
+  if (tiles < target && g.K > 4 * BK) {
+    long long want = (target + tiles - 1) / tiles;
+    long long maxs = g.K / (4 * BK);
+    splitK = int(want < maxs ? want : maxs);
+    if (splitK < 1) splitK = 1;
+  }
+  kchunk = (g.K + splitK - 1) / splitK;
+  kchunk = ((kchunk + BK - 1) / BK) * BK;
+  splitK = (g.K + kchunk - 1) / kchunk;
+  if (splitK < 1) splitK = 1;
+}
+
+}  // namespace
+
+size_t zgemm64_workspace(const GemmDesc& g, int num_sms) {
+  int splitK, kchunk;
+  choose_split(g, num_sms, splitK, kchunk);
+  if (splitK <= 1) return 0;
+  return sizeof(double2) * (size_t)splitK * g.batch * (size_t)g.M * g.N;
+}
+
+int zgemm64(const Launch& L, const GemmDesc& g, void* workspace, size_t ws_bytes) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return 0;
+  if (g.K <= 0) return TEVO_EINVAL;
+  int splitK, kchunk;
+  choose_split(g, L.num_sms, splitK, kchunk);
+  size_t need = splitK > 1 ? sizeof(double2) * (size_t)splitK * g.batch * (size_t)g.M * g.N : 0;
+  if (need > ws_bytes) {
+    splitK = 1;
+    kchunk = ((g.K + BK - 1) / BK) * BK;
+  }
+  if ((long long)g.batch * splitK > 65535 || (g.M + BM - 1) / BM > 65535) return TEVO_ESHAPE;
+  GemmKArgs p{g, splitK, kchunk, reinterpret_cast<double2*>(workspace)};
+  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch * splitK);
+  if (g.conjA && g.conjB)
+    zgemm_kernel<true, true><<<grid, GEMM_THREADS, 0, L.stream>>>(p);
+  else if (g.conjA)
+    zgemm_kernel<true, false><<<grid, GEMM_THREADS, 0, L.stream>>>(p);
+  else if (g.conjB)
+    zgemm_kernel<false, true><<<grid, GEMM_THREADS, 0, L.stream>>>(p);
+  else
+    zgemm_kernel<false, false><<<grid, GEMM_THREADS, 0, L.stream>>>(p);
+  ++*L.launches;
+  if (splitK > 1) {
+    long long total = (long long)g.M * g.N * g.batch;
+    int blocks = int(std::min<long long>((total + 255) / 256, 8LL * L.num_sms));
+    zgemm_reduce_kernel<<<blocks, 256, 0, L.stream>>>(g, splitK, p.partial);
+    ++*L.launches;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int QR_THREADS = 128;
+constexpr double DEFLATE = 2.2737367544323206e-13;  // 2^-42
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  const int nw = blockDim.x >> 5;
+  for (int w = 0; w < nw; ++w) s += red[w];  // fixed order: identical in every thread
+  return s;
+}
+
+__device__ double2 block_csum(double2 v, double* red) {
+  double a = block_sum(v.x, red);
+  double b = block_sum(v.y, red + 32);
+  return make_double2(a, b);
+}
+
+// sum |A|^2 of the m x n matrix (partial sums per block, fixed grid)
+__global__ void frob_partial_kernel(const double2* A, long long n, double* part) {
+  __shared__ double red[64];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double2 v = A[i];
+    s = fma(v.x, v.x, s);
+    s = fma(v.y, v.y, s);
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void sum_partials_kernel(const double* part, int np, double* out) {
+  __shared__ double red[64];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+constexpr int FROB_BLOCKS = 256;
+
+// One column step k. Every CTA recomputes the reflector of column k from the
+// (already updated) column, then applies H_k^H to one trailing column j.
+// CTA 0 with j == k+1 (or the only CTA when k == n-1) records v, tau, beta.
+__global__ void qr_step_kernel(double2* A, int m, int n, int k, double2* V, double2* tau,
+                               double2* beta, const double* frob2) {
+  extern __shared__ double2 v[];  // m - k entries
+  __shared__ double red[64];
+  const int len = m - k;
+  const double2* x = A + (long long)k * m + k;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < len; r += blockDim.x) {
+    double2 a = x[r];
+    v[r] = a;
+    s = fma(a.x, a.x, s);
+    s = fma(a.y, a.y, s);
+  }
+  const double nrm2 = block_sum(s, red);
+  const double nrm = sqrt(nrm2);
+  const double tol = DEFLATE * sqrt(*frob2);
+  const double2 alpha = v[0];
+  const bool deflate = (nrm <= tol) || (nrm == 0.0);
+  double2 t = make_double2(0.0, 0.0);
+  double b = 0.0;
+  if (!deflate) {
+    b = alpha.x >= 0.0 ? -nrm : nrm;
+    t = make_double2((b - alpha.x) / b, -alpha.y / b);
+    // v = x / (alpha - beta), v[0] = 1
+    double2 den = make_double2(alpha.x - b, alpha.y);
+    double dd = den.x * den.x + den.y * den.y;
+    double2 inv = make_double2(den.x / dd, -den.y / dd);
+    __syncthreads();
+    for (int r = threadIdx.x; r < len; r += blockDim.x) v[r] = (r == 0) ? make_double2(1.0, 0.0) : cmul(v[r], inv);
+  }
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) {
+      tau[k] = t;
+      beta[k] = deflate ? alpha : make_double2(b, 0.0);
+    }
+    double2* Vk = V + (long long)k * m;
+    for (int r = threadIdx.x; r < m; r += blockDim.x)
+      Vk[r] = (r < k) ? make_double2(0.0, 0.0) : (deflate ? make_double2(r == k ? 1.0 : 0.0, 0.0) : v[r - k]);
+  }
+  if (deflate) return;
+  const int j = k + 1 + blockIdx.x;
+  if (j >= n) return;
+  double2* col = A + (long long)j * m + k;
+  // w = v^H col
+  double2 w = make_double2(0.0, 0.0);
+  for (int r = threadIdx.x; r < len; r += blockDim.x) w = cfma(cconj(v[r]), col[r], w);
+  w = block_csum(w, red);
+  // col -= conj(t) v w
+  const double2 f = cmul(cconj(t), w);
+  for (int r = threadIdx.x; r < len; r += blockDim.x) {
+    double2 c = col[r];
+    double2 d = cmul(v[r], f);
+    col[r] = make_double2(c.x - d.x, c.y - d.y);
+  }
+}
+
+// Q column c = H_0 H_1 ... H_c e_c, one CTA per column; q kept in shared memory
+__global__ void qr_form_q_kernel(const double2* V, const double2* tau, int m, int n, double2* Q,
+                                 long long sQr, long long sQc) {
+  extern __shared__ double2 q[];
+  __shared__ double red[64];
+  const int c = blockIdx.x;
+  for (int r = threadIdx.x; r < m; r += blockDim.x) q[r] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  for (int k = c; k >= 0; --k) {
+    const double2 t = tau[k];
+    if (t.x == 0.0 && t.y == 0.0) continue;  // uniform across the block
+    const double2* vk = V + (long long)k * m;
+    double2 w = make_double2(0.0, 0.0);
+    for (int r = k + threadIdx.x; r < m; r += blockDim.x) w = cfma(cconj(vk[r]), q[r], w);
+    w = block_csum(w, red);
+    const double2 f = cmul(t, w);
+    for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
+      double2 d = cmul(vk[r], f);
+      q[r] = make_double2(q[r].x - d.x, q[r].y - d.y);
+    }
+    __syncthreads();
+  }
+  for (int r = threadIdx.x; r < m; r += blockDim.x) Q[(long long)r * sQr + (long long)c * sQc] = q[r];
+}
+
+__global__ void qr_extract_r_kernel(const double2* A, const double2* beta, int m, int n, double2* R) {
+  long long total = (long long)n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int r = int(idx / n), c = int(idx % n);
+    double2 v = make_double2(0.0, 0.0);
+    if (r == c)
+      v = beta[r];
+    else if (r < c)
+      v = A[(long long)c * m + r];
+    R[idx] = v;
+  }
+}
+
+}  // namespace
+
+size_t qr64_scratch_bytes(int m, int n) { return sizeof(double) * (FROB_BLOCKS + 8); }
+
+int qr64_factor(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_, z64* beta_, void* scratch) {
+  if (m < n || n <= 0) return TEVO_ESHAPE;
+  double2* A = reinterpret_cast<double2*>(A_);
+  double2* V = reinterpret_cast<double2*>(V_);
+  double2* tau = reinterpret_cast<double2*>(tau_);
+  double2* beta = reinterpret_cast<double2*>(beta_);
+  double* part = reinterpret_cast<double*>(scratch);
+  double* frob2 = part + FROB_BLOCKS;
+  frob_partial_kernel<<<FROB_BLOCKS, 256, 0, L.stream>>>(A, (long long)m * n, part);
+  sum_partials_kernel<<<1, 256, 0, L.stream>>>(part, FROB_BLOCKS, frob2);
+  *L.launches += 2;
+  const size_t smem = sizeof(double2) * (size_t)m;
+  if (smem > 48 * 1024) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(qr_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(qr_form_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_set = true;
+    }
+  }
+  for (int k = 0; k < n; ++k) {
+    int grid = n - k - 1;
+    if (grid < 1) grid = 1;
+    qr_step_kernel<<<grid, QR_THREADS, smem, L.stream>>>(A, m, n, k, V, tau, beta, frob2);
+    ++*L.launches;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int qr64_form_q(const Launch& L, const z64* V, const z64* tau, int m, int n, z64* Q, long long sQr,
+                long long sQc) {
+  const size_t smem = sizeof(double2) * (size_t)m;
+  qr_form_q_kernel<<<n, QR_THREADS, smem, L.stream>>>(reinterpret_cast<const double2*>(V),
+                                                      reinterpret_cast<const double2*>(tau), m, n,
+                                                      reinterpret_cast<double2*>(Q), sQr, sQc);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int qr64_extract_r(const Launch& L, const z64* A, const z64* beta, int m, int n, z64* R) {
+  long long total = (long long)n * n;
+  int blocks = int(std::min<long long>((total + 255) / 256, 4LL * L.num_sms));
+  qr_extract_r_kernel<<<blocks, 256, 0, L.stream>>>(reinterpret_cast<const double2*>(A),
+                                                    reinterpret_cast<const double2*>(beta), m, n,
+                                                    reinterpret_cast<double2*>(R));
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// layout and reduction helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void mirror_kernel(const double2* in, double2* out, int na, int d, int nb) {
+  long long total = (long long)na * d * nb;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    // idx enumerates out[b][s][a]
+    int a = int(idx % na);
+    long long t = idx / na;
+    int s = int(t % d);
+    int b = int(t / d);
+    out[idx] = in[((long long)a * d + s) * nb + b];
+  }
+}
+
+__global__ void copy2d_kernel(const double2* src, long long sr, long long sc, double2* dst, long long dr,
+                              long long dc, int rows, int cols) {
+  long long total = (long long)rows * cols;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int r = int(idx / cols), c = int(idx % cols);
+    dst[r * dr + c * dc] = src[r * sr + c * sc];
+  }
+}
+
+__global__ void fill_kernel(double2* dst, long long n, double re, double im) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    dst[idx] = make_double2(re, im);
+}
+
+__global__ void normalize_kernel(double2* x, long long n, const double* nrm2, double* lognorm, int* flag) {
+  const double s2 = *nrm2;
+  const bool bad = !(s2 > 0.0) || !isfinite(s2);
+  if (bad) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *flag = 1;
+    return;
+  }
+  const double inv = 1.0 / sqrt(s2);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *lognorm += 0.5 * log(s2);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    double2 v = x[idx];
+    x[idx] = make_double2(v.x * inv, v.y * inv);
+  }
+}
+
+__global__ void dotu_partial_kernel(const double2* a, const double2* b, long long n, double* part) {
+  __shared__ double red[64];
+  double2 s = make_double2(0.0, 0.0);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    s = cfma(a[i], b[i], s);
+  double2 t = block_csum(s, red);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = t.x;
+    part[2 * blockIdx.x + 1] = t.y;
+  }
+}
+
+__global__ void dotu_final_kernel(const double* part, int np, double2* out) {
+  __shared__ double red[64];
+  double2 s = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    s.x += part[2 * i];
+    s.y += part[2 * i + 1];
+  }
+  double2 t = block_csum(s, red);
+  if (threadIdx.x == 0) *out = t;
+}
+
+__global__ void rescale_kernel(double2* E, long long n, const double* nrm2, double* logacc) {
+  const double s2 = *nrm2;
+  if (!(s2 > 0.0) || !isfinite(s2)) return;
+  const double inv = 1.0 / sqrt(s2);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *logacc += 0.5 * log(s2);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    double2 v = E[idx];
+    E[idx] = make_double2(v.x * inv, v.y * inv);
+  }
+}
+
+int grid_for(long long n, int num_sms) {
+  long long b = (n + 255) / 256;
+  long long cap = 8LL * num_sms;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return int(b);
+}
+
+}  // namespace
+
+int mirror_site64(const Launch& L, const z64* in, z64* out, int na, int d, int nb) {
+  long long total = (long long)na * d * nb;
+  mirror_kernel<<<grid_for(total, L.num_sms), 256, 0, L.stream>>>(reinterpret_cast<const double2*>(in),
+                                                                    reinterpret_cast<double2*>(out), na, d, nb);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int copy2d64(const Launch& L, const z64* src, long long sr, long long sc, z64* dst, long long dr, long long dc,
+             int rows, int cols) {
+  long long total = (long long)rows * cols;
+  if (total <= 0) return 0;
+  copy2d_kernel<<<grid_for(total, L.num_sms), 256, 0, L.stream>>>(reinterpret_cast<const double2*>(src), sr, sc,
+                                                                   reinterpret_cast<double2*>(dst), dr, dc, rows,
+                                                                   cols);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int fill64(const Launch& L, z64* dst, size_t n, double re, double im) {
+  if (n == 0) return 0;
+  fill_kernel<<<grid_for((long long)n, L.num_sms), 256, 0, L.stream>>>(reinterpret_cast<double2*>(dst),
+                                                                       (long long)n, re, im);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int norm2_64(const Launch& L, const z64* x, size_t n, double* out, double* scratch) {
+  frob_partial_kernel<<<FROB_BLOCKS, 256, 0, L.stream>>>(reinterpret_cast<const double2*>(x), (long long)n,
+                                                         scratch);
+  sum_partials_kernel<<<1, 256, 0, L.stream>>>(scratch, FROB_BLOCKS, out);
+  *L.launches += 2;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int normalize64(const Launch& L, z64* x, size_t n, const double* nrm2, double* lognorm, int* flag) {
+  normalize_kernel<<<grid_for((long long)n, L.num_sms), 256, 0, L.stream>>>(reinterpret_cast<double2*>(x),
+                                                                             (long long)n, nrm2, lognorm, flag);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int dotu64(const Launch& L, const z64* a, const z64* b, size_t n, z64* out, double* scratch) {
+  dotu_partial_kernel<<<FROB_BLOCKS, 256, 0, L.stream>>>(reinterpret_cast<const double2*>(a),
+                                                         reinterpret_cast<const double2*>(b), (long long)n, scratch);
+  dotu_final_kernel<<<1, 256, 0, L.stream>>>(scratch, FROB_BLOCKS, reinterpret_cast<double2*>(out));
+  *L.launches += 2;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int rescale64(const Launch& L, z64* E, size_t n, double* logacc, double* scratch) {
+  double* nrm2 = scratch + 2 * FROB_BLOCKS;
+  frob_partial_kernel<<<FROB_BLOCKS, 256, 0, L.stream>>>(reinterpret_cast<const double2*>(E), (long long)n,
+                                                         scratch);
+  sum_partials_kernel<<<1, 256, 0, L.stream>>>(scratch, FROB_BLOCKS, nrm2);
+  rescale_kernel<<<grid_for((long long)n, L.num_sms), 256, 0, L.stream>>>(reinterpret_cast<double2*>(E),
+                                                                           (long long)n, nrm2, logacc);
+  *L.launches += 3;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+}  // namespace tevo

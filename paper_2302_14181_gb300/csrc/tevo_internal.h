@@ -1,0 +1,85 @@
+// Internal declarations shared by the translation units of libtevo.
+#pragma once
+
+#include <complex>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/tevo.h"
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#else
+struct CUstream_st;
+typedef CUstream_st* cudaStream_t;
+#endif
+
+namespace tevo {
+
+// host MPO construction (mpo_build.cpp)
+int build_mpo_host(int L, int d, int chi, const double* A, const double* B, const double* C,
+                   const double* Dh, int N, double tau_re, double tau_im, int variant,
+                   std::vector<std::vector<std::complex<double>>>& sites, std::vector<int>& wl,
+                   std::vector<int>& wr);
+
+// complex fp64 as two doubles
+struct z64 {
+  double x, y;
+};
+
+// Strided batched complex GEMM description: C[b](m,n) = alpha * sum_k op(A)[b](m,k) op(B)[b](k,n)
+// (+ beta * C). Strides are in complex elements; op() conjugates when conj* is set.
+struct GemmDesc {
+  const void* A;
+  const void* B;
+  void* C;
+  int M, N, K, batch;
+  long long sAb, sAm, sAk;
+  long long sBb, sBk, sBn;
+  long long sCb, sCm, sCn;
+  int conjA, conjB;
+  double alpha_re, alpha_im, beta_re, beta_im;
+};
+
+// launch-side context passed to the kernel wrappers
+struct Launch {
+  cudaStream_t stream;
+  long long* launches;  // incremented per kernel launch
+  int num_sms;
+};
+
+// ---------------------------------------------------------------------------
+// fp64 kernels (k_fp64.cu)
+// ---------------------------------------------------------------------------
+// workspace bytes needed by zgemm64 for this description (split-K partials)
+size_t zgemm64_workspace(const GemmDesc& g, int num_sms);
+int zgemm64(const Launch& L, const GemmDesc& g, void* workspace, size_t ws_bytes);
+
+// Householder QR of a column-major m x n matrix (ld = m), in place.
+// V (m x n col-major) receives the reflectors, tau/beta (n) the scalars.
+// scratch: >= qr64_scratch_bytes(m, n).
+size_t qr64_scratch_bytes(int m, int n);
+int qr64_factor(const Launch& L, z64* A, int m, int n, z64* V, z64* tau, z64* beta, void* scratch);
+// explicit thin Q (m x n) written with element (r, c) at Q[r * sQr + c * sQc]
+int qr64_form_q(const Launch& L, const z64* V, const z64* tau, int m, int n, z64* Q, long long sQr,
+                long long sQc);
+// R (n x n) from the factored A and beta: dense upper-triangular, row-major
+int qr64_extract_r(const Launch& L, const z64* A, const z64* beta, int m, int n, z64* R);
+
+// out[b][s][a] = in[a][s][b] for in of shape [na][d][nb]
+int mirror_site64(const Launch& L, const z64* in, z64* out, int na, int d, int nb);
+// dst(r, c) = src(r, c) for strided 2-D views (complex)
+int copy2d64(const Launch& L, const z64* src, long long sr, long long sc, z64* dst, long long dr,
+             long long dc, int rows, int cols);
+int fill64(const Launch& L, z64* dst, size_t n, double re, double im);
+// sum |x|^2 over n entries into *out (device), deterministic two-pass
+int norm2_64(const Launch& L, const z64* x, size_t n, double* out, double* scratch);
+// x /= sqrt(*nrm2); *lognorm += log(sqrt(*nrm2)); flags nonfinite into *flag
+int normalize64(const Launch& L, z64* x, size_t n, const double* nrm2, double* lognorm, int* flag);
+// sum_i a[i] * b[i] (no conjugation) into *out (device, complex)
+int dotu64(const Launch& L, const z64* a, const z64* b, size_t n, z64* out, double* scratch);
+// E /= ||E||_F, *logacc += log ||E||_F (overlap transfer rescaling)
+int rescale64(const Launch& L, z64* E, size_t n, double* logacc, double* scratch);
+
+}  // namespace tevo
