@@ -171,12 +171,42 @@ int measure_local(tevo_mps psi, int nops, const double* ops, double* out);
  */
 int mps_overlap(tevo_mps a, tevo_mps b, double* log_abs, double* phase);
 
+/*
+ * tevo_gemm -- the complex contraction primitive of the sweep on its own:
+ * C[m][n] = sum_k A[m][k] B[n][k] for complex fp64 device arrays A [M][K],
+ * B [N][K] (row-major, k contiguous) and C [M][N] (row-major), computed in the
+ * given precision: TEVO_FP64 on the fp64 pipe, the others on the tensor cores
+ * (operands rounded/split into the precision's planes, fp32 accumulation, fp64
+ * result). Device pointers, aligned to 16 bytes; temporary device memory comes
+ * from the context's allocator and is released before returning.
+ * Errors: TEVO_EINVAL, TEVO_ENOMEM, TEVO_ECUDA, TEVO_ETIMEOUT. Synchronises.
+ */
+int tevo_gemm(tevo_ctx ctx, int precision, int M, int N, int K, const double* A, const double* B, double* C);
+
 /* name of an error code */
 const char* tevo_strerror(int code);
 
 /* number of kernels this library launched on the context since creation or the
  * last reset (host-side count of launches issued by the library) */
 int tevo_launch_count(tevo_ctx ctx, long long* count, int reset);
+
+/*
+ * Event-timed kernel profile (diagnostics for the roofline figures). While
+ * enabled, the library records a CUDA event pair on the context stream around
+ * every launch of the kernel classes below, with the algorithmic flop and byte
+ * count of that launch (from its shape: useful complex multiply-adds x 8 flops;
+ * operand reads + output write once each). tevo_prof_read synchronises the
+ * stream, returns the totals of one class since the last read of that class,
+ * and clears them.
+ */
+#define TEVO_PROF_GEMM64 0   /* fp64 complex GEMM (main kernel, split-K partials included) */
+#define TEVO_PROF_GEMMTC 1   /* tensor-core complex GEMM */
+#define TEVO_PROF_QR 2       /* Householder factorisation of one matrix (all its column steps) */
+#define TEVO_PROF_FORMQ 3    /* explicit thin Q */
+#define TEVO_PROF_CLASSES 4
+int tevo_prof_enable(tevo_ctx ctx, int enable);
+int tevo_prof_read(tevo_ctx ctx, int cls, double* ms_total, long long* launches, double* flops_total,
+                   double* bytes_total);
 
 #ifdef __cplusplus
 }

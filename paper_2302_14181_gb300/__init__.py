@@ -88,6 +88,17 @@ class Context:
         self._torch_cb = (_alloc, _free)
         _lib.check(_lib.lib.tevo_ctx_set_allocator(self.handle, _alloc, _free, None))
 
+    def prof_enable(self, on=True):
+        _lib.check(_lib.lib.tevo_prof_enable(self.handle, int(on)))
+
+    def prof_read(self, cls):
+        """(total ms, launches, algorithmic flops, algorithmic bytes) of one kernel class."""
+        ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_longlong()
+        _lib.check(_lib.lib.tevo_prof_read(self.handle, int(cls), ctypes.byref(ms), ctypes.byref(n),
+                                           ctypes.byref(fl), ctypes.byref(by)))
+        return ms.value, n.value, fl.value, by.value
+
     def launch_count(self, reset=False):
         n = ctypes.c_longlong()
         _lib.check(_lib.lib.tevo_launch_count(self.handle, ctypes.byref(n), int(reset)))

@@ -17,6 +17,7 @@ lib = ctypes.CDLL(LIB_PATH)
 
 FP64, TF32, TF32X3, BF16X3 = 0, 1, 2, 3
 MPO_PLAIN, MPO_EXACT, MPO_EXTENDED, MPO_FULL = 0, 1, 2, 3
+PROF_GEMM64, PROF_GEMMTC, PROF_QR, PROF_FORMQ = 0, 1, 2, 3
 
 
 class tevo_ctx(ctypes.c_void_p):
@@ -58,6 +59,9 @@ _SIGS = {
     "evolve_step": [tevo_mps, tevo_mpo, _d, _d, _i, _i, _i],
     "measure_local": [tevo_mps, _i, _pd, _pd],
     "mps_overlap": [tevo_mps, tevo_mps, _pd, _pd],
+    "tevo_gemm": [tevo_ctx, _i, _i, _i, _i, _p, _p, _p],
+    "tevo_prof_enable": [tevo_ctx, _i],
+    "tevo_prof_read": [tevo_ctx, _i, _pd, ctypes.POINTER(ctypes.c_longlong), _pd, _pd],
 }
 
 for _name, _args in _SIGS.items():

@@ -39,6 +39,7 @@ struct tevo_ctx_s {
   long long launches = 0;
   int device = 0;
   int num_sms = 1;
+  Prof prof;
 };
 
 namespace {
@@ -86,7 +87,7 @@ int ensure(tevo_ctx c, Buf& b, size_t bytes) {
   return dalloc(c, b, bytes);
 }
 
-Launch launch_of(tevo_ctx c) { return Launch{c->stream, &c->launches, c->num_sms}; }
+Launch launch_of(tevo_ctx c) { return Launch{c->stream, &c->launches, c->num_sms, &c->prof}; }
 
 inline z64* zp(const Buf& b) { return reinterpret_cast<z64*>(b.p); }
 
@@ -357,6 +358,11 @@ extern "C" int tevo_ctx_create(void* stream, tevo_ctx* out) {
 
 extern "C" int tevo_ctx_destroy(tevo_ctx c) {
   if (!c) return TEVO_EINVAL;
+  for (auto& r : c->prof.recs) {
+    cudaEventDestroy(reinterpret_cast<cudaEvent_t>(r.e0));
+    cudaEventDestroy(reinterpret_cast<cudaEvent_t>(r.e1));
+  }
+  for (void* e : c->prof.pool) cudaEventDestroy(reinterpret_cast<cudaEvent_t>(e));
   delete c;
   return 0;
 }
@@ -379,6 +385,66 @@ extern "C" int tevo_launch_count(tevo_ctx c, long long* count, int reset) {
   if (!c || !count) return TEVO_EINVAL;
   *count = c->launches;
   if (reset) c->launches = 0;
+  return 0;
+}
+
+namespace tevo {
+int Prof::begin(cudaStream_t s, int cls, double flops, double bytes) {
+  if (!on) return -1;
+  auto get = [&]() -> void* {
+    if (!pool.empty()) {
+      void* e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  };
+  void* e0 = get();
+  void* e1 = get();
+  if (!e0 || !e1) return -1;
+  cudaEventRecord(reinterpret_cast<cudaEvent_t>(e0), s);
+  recs.push_back(Rec{cls, e0, e1, flops, bytes});
+  return int(recs.size()) - 1;
+}
+void Prof::end(cudaStream_t s, int idx) {
+  if (idx < 0) return;
+  cudaEventRecord(reinterpret_cast<cudaEvent_t>(recs[idx].e1), s);
+}
+}  // namespace tevo
+
+extern "C" int tevo_prof_enable(tevo_ctx c, int enable) {
+  if (!c) return TEVO_EINVAL;
+  c->prof.on = enable != 0;
+  return 0;
+}
+
+extern "C" int tevo_prof_read(tevo_ctx c, int cls, double* ms, long long* n, double* flops, double* bytes) {
+  if (!c || !ms || !n || !flops || !bytes || cls < 0 || cls >= TEVO_PROF_CLASSES) return TEVO_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TEVO_ECUDA;
+  *ms = 0;
+  *n = 0;
+  *flops = 0;
+  *bytes = 0;
+  std::vector<Prof::Rec> keep;
+  for (auto& r : c->prof.recs) {
+    if (r.cls != cls) {
+      keep.push_back(r);
+      continue;
+    }
+    float t = 0;
+    if (cudaEventElapsedTime(&t, reinterpret_cast<cudaEvent_t>(r.e0), reinterpret_cast<cudaEvent_t>(r.e1)) !=
+        cudaSuccess)
+      return TEVO_ECUDA;
+    *ms += t;
+    *n += 1;
+    *flops += r.flops;
+    *bytes += r.bytes;
+    c->prof.pool.push_back(r.e0);
+    c->prof.pool.push_back(r.e1);
+  }
+  c->prof.recs.swap(keep);
   return 0;
 }
 
@@ -638,9 +704,11 @@ extern "C" int evolve_step(tevo_mps s, tevo_mpo W, double tau_re, double tau_im,
   for (int k = 0; k < n64; ++k) TRY(sweep64(s, W));
   TRY(centre64(s, W));
   TRY(finish_step(s));
-  int flag = 0;
+  int flag = 0, tflag = 0;
   TRYCUDA(cudaMemcpyAsync(&flag, scal(s, 4), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  if (mixed) TRY(mixed_error_flag(c, s, &tflag));
   TRYCUDA(cudaStreamSynchronize(c->stream));
+  if (tflag) return TEVO_ETIMEOUT;
   if (flag) return TEVO_ENONFINITE;
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
 }
@@ -763,6 +831,23 @@ extern "C" int measure_local(tevo_mps s, int nops, const double* ops, double* ou
   };
   if (!e) e = run();
   cleanup();
+  return e;
+}
+
+extern "C" int tevo_gemm(tevo_ctx c, int precision, int M, int N, int K, const double* A, const double* B,
+                         double* C) {
+  if (!c || !A || !B || !C || M < 1 || N < 1 || K < 1) return TEVO_EINVAL;
+  if (precision < TEVO_FP64 || precision > TEVO_BF16X3) return TEVO_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15)
+    return TEVO_EINVAL;
+  if (precision != TEVO_FP64) return mixed_gemm(c, precision, M, N, K, A, B, C);
+  Buf ws;
+  GemmDesc g = gd(A, 0, K, 1, B, 0, 1, K, C, 0, N, 1, M, N, K, 1);
+  size_t need = zgemm64_workspace(g, c->num_sms);
+  int e = dalloc(c, ws, need);
+  if (!e) e = zgemm64(launch_of(c), g, ws.p, ws.bytes);
+  if (!e && cudaStreamSynchronize(c->stream) != cudaSuccess) e = TEVO_ECUDA;
+  dfree(c, ws);
   return e;
 }
 

@@ -200,6 +200,10 @@ int zgemm64(const Launch& L, const GemmDesc& g, void* workspace, size_t ws_bytes
   if ((long long)g.batch * splitK > 65535 || (g.M + BM - 1) / BM > 65535) return TEVO_ESHAPE;
   GemmKArgs p{g, splitK, kchunk, reinterpret_cast<double2*>(workspace)};
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch * splitK);
+  const double flops = 8.0 * g.M * (double)g.N * g.K * g.batch;
+  const double bytes = 16.0 * ((double)g.M * g.K * (g.sAb ? g.batch : 1) + (double)g.K * g.N * (g.sBb ? g.batch : 1) +
+                               (double)g.M * g.N * g.batch);
+  int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_GEMM64, flops, bytes) : -1;
   if (g.conjA && g.conjB)
     zgemm_kernel<true, true><<<grid, GEMM_THREADS, 0, L.stream>>>(p);
   else if (g.conjA)
@@ -215,6 +219,7 @@ int zgemm64(const Launch& L, const GemmDesc& g, void* workspace, size_t ws_bytes
     zgemm_reduce_kernel<<<blocks, 256, 0, L.stream>>>(g, splitK, p.partial);
     ++*L.launches;
   }
+  if (L.prof) L.prof->end(L.stream, pr);
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
 }
 
@@ -379,6 +384,8 @@ int qr64_factor(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_, z64*
   double2* beta = reinterpret_cast<double2*>(beta_);
   double* part = reinterpret_cast<double*>(scratch);
   double* frob2 = part + FROB_BLOCKS;
+  const double qflops = 8.0 * (4.0 * (double)m * n * n - 4.0 / 3.0 * (double)n * n * n);
+  int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_QR, qflops, 32.0 * (double)m * n) : -1;
   frob_partial_kernel<<<FROB_BLOCKS, 256, 0, L.stream>>>(A, (long long)m * n, part);
   sum_partials_kernel<<<1, 256, 0, L.stream>>>(part, FROB_BLOCKS, frob2);
   *L.launches += 2;
@@ -397,16 +404,20 @@ int qr64_factor(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_, z64*
     qr_step_kernel<<<grid, QR_THREADS, smem, L.stream>>>(A, m, n, k, V, tau, beta, frob2);
     ++*L.launches;
   }
+  if (L.prof) L.prof->end(L.stream, pr);
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
 }
 
 int qr64_form_q(const Launch& L, const z64* V, const z64* tau, int m, int n, z64* Q, long long sQr,
                 long long sQc) {
   const size_t smem = sizeof(double2) * (size_t)m;
+  const double fflops = 8.0 * (4.0 * (double)m * n * n - 4.0 / 3.0 * (double)n * n * n) / 2.0;
+  int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_FORMQ, fflops, 32.0 * (double)m * n) : -1;
   qr_form_q_kernel<<<n, QR_THREADS, smem, L.stream>>>(reinterpret_cast<const double2*>(V),
                                                       reinterpret_cast<const double2*>(tau), m, n,
                                                       reinterpret_cast<double2*>(Q), sQr, sQc);
   ++*L.launches;
+  if (L.prof) L.prof->end(L.stream, pr);
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
 }
 

@@ -42,11 +42,28 @@ struct GemmDesc {
   double alpha_re, alpha_im, beta_re, beta_im;
 };
 
+// event-timed profile of kernel classes (TEVO_PROF_*)
+struct Prof {
+  bool on = false;
+  struct Rec {
+    int cls;
+    void* e0;
+    void* e1;
+    double flops, bytes;
+  };
+  std::vector<Rec> recs;
+  std::vector<void*> pool;  // cudaEvent_t
+  // returns an index into recs (or -1 when off); the caller launches between begin/end
+  int begin(cudaStream_t s, int cls, double flops, double bytes);
+  void end(cudaStream_t s, int idx);
+};
+
 // launch-side context passed to the kernel wrappers
 struct Launch {
   cudaStream_t stream;
   long long* launches;  // incremented per kernel launch
   int num_sms;
+  Prof* prof;
 };
 
 // ---------------------------------------------------------------------------
