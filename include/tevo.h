@@ -49,6 +49,10 @@ extern "C" {
 #define TEVO_TF32 1      /* tcgen05 kind::tf32, fp32 accumulate; fp64 QR and final sweep */
 #define TEVO_TF32X3 2    /* three-pass split tf32 (hi*hi + hi*lo + lo*hi); fp64 QR and final sweep */
 #define TEVO_BF16X3 3    /* three-pass split bf16 (hi*hi + hi*lo + lo*hi); fp64 QR and final sweep */
+/* OR-ed into a low-precision form: every sweep (and the centre) on the tensor
+ * cores, no fp64 rebuild or fp64 sweep; the QR, the norm and the reductions stay
+ * fp64. Not the paper's recipe: an extra form for accuracy/speed studies. */
+#define TEVO_TC_ONLY 0x100
 
 /* variants of the MPO construction (Secs. 3-6 of the paper) */
 #define TEVO_MPO_PLAIN 0     /* Algorithm 1 only (Eq. W1 at N = 1, Eq. W2 at N = 2) */

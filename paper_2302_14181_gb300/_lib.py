@@ -16,6 +16,7 @@ if not os.path.exists(LIB_PATH):
 lib = ctypes.CDLL(LIB_PATH)
 
 FP64, TF32, TF32X3, BF16X3 = 0, 1, 2, 3
+TC_ONLY = 0x100
 MPO_PLAIN, MPO_EXACT, MPO_EXTENDED, MPO_FULL = 0, 1, 2, 3
 PROF_GEMM64, PROF_GEMMTC, PROF_QR, PROF_FORMQ = 0, 1, 2, 3
 

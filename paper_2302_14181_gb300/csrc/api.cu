@@ -670,7 +670,10 @@ extern "C" int mps_destroy(tevo_mps s) {
 // ---------------------------------------------------------------------------
 extern "C" int evolve_step(tevo_mps s, tevo_mpo W, double tau_re, double tau_im, int D, int sweeps, int precision) {
   if (!s || !W || sweeps < 1) return TEVO_EINVAL;
+  const bool tc_only = (precision & TEVO_TC_ONLY) != 0;
+  precision &= ~TEVO_TC_ONLY;
   if (precision < TEVO_FP64 || precision > TEVO_BF16X3) return TEVO_EINVAL;
+  if (tc_only && precision == TEVO_FP64) return TEVO_EINVAL;
   if (W->L != s->L || W->d != s->d) return TEVO_ESHAPE;
   if (D != s->D) return TEVO_ESHAPE;
   if (tau_re != W->tau_re || tau_im != W->tau_im) return TEVO_ETAU;
@@ -690,19 +693,26 @@ extern "C" int evolve_step(tevo_mps s, tevo_mpo W, double tau_re, double tau_im,
     TRY(right_canonicalize(s, s->Anew));
     bra = &s->Anew;
   }
-  const bool mixed = precision != TEVO_FP64 && sweeps > 1;
+  const bool mixed = precision != TEVO_FP64 && (sweeps > 1 || tc_only);
   if (mixed) {
     TRY(mixed_prepare(c, W, s, precision));
     TRY(mixed_build_right_envs(c, W, s, bra == &s->Anew, precision));
-    for (int k = 0; k < sweeps - 1; ++k) TRY(mixed_sweep(c, W, s, precision));
-    // fp64 rebuild of the right environments from the fitted phi, then one fp64 sweep
-    TRY(build_right_envs64(s, W, s->Anew, s->A));
+    const int nlp = tc_only ? sweeps : sweeps - 1;
+    for (int k = 0; k < nlp; ++k) TRY(mixed_sweep(c, W, s, precision));
+    if (!tc_only) {
+      // fp64 rebuild of the right environments from the fitted phi, then one fp64 sweep
+      TRY(build_right_envs64(s, W, s->Anew, s->A));
+    }
   } else {
     TRY(build_right_envs64(s, W, *bra, s->A));
   }
-  const int n64 = mixed ? 1 : sweeps;
-  for (int k = 0; k < n64; ++k) TRY(sweep64(s, W));
-  TRY(centre64(s, W));
+  if (tc_only) {
+    TRY(mixed_centre(c, W, s, precision));
+  } else {
+    const int n64 = mixed ? 1 : sweeps;
+    for (int k = 0; k < n64; ++k) TRY(sweep64(s, W));
+    TRY(centre64(s, W));
+  }
   TRY(finish_step(s));
   int flag = 0, tflag = 0;
   TRYCUDA(cudaMemcpyAsync(&flag, scal(s, 4), sizeof(int), cudaMemcpyDeviceToHost, c->stream));

@@ -1,0 +1,496 @@
+// Tensor-core complex GEMM for sm_103a: tcgen05.mma with accumulators in tensor
+// memory, operands staged in shared memory by TMA (cp.async.bulk.tensor), one
+// elected thread issuing the MMAs, mbarrier pipeline between the TMA producer
+// warp and the MMA warp.
+//
+//   C[m][n] = sum_k A[m][k] * B[n][k]          (complex, both operands K-major)
+//
+// A complex operand is stored as "planes" of a real type: for the split forms
+// (bf16x3, tf32x3) the planes are re_hi, re_lo, im_hi, im_lo with x = hi + lo;
+// for plain tf32 they are re, im. A product of planes is one real MMA, so one
+// complex K-step issues
+//   Cr += Ar.Br - Ai.Bi,  Ci += Ar.Bi + Ai.Br
+// per pair of split terms (hi.hi + hi.lo + lo.hi for the split forms: 12 MMAs;
+// 4 MMAs for plain tf32), the minus sign through the negate-A bit of the
+// instruction descriptor. Accumulation is fp32 in tensor memory.
+//
+// Each operand is a 4-D tensor [k_in, k_out, rows, planes] (k_in innermost).
+// The K loop runs over (k_out, k_in chunk) pairs, so a reduction index that
+// is itself two tensor modes with a padded inner mode (an environment's
+// (w, psi) legs) is read through TMA bounds checks instead of padding.
+//
+// CTA tile 128 (M) x 256 (N); Cr occupies tensor-memory columns [0, 256) and
+// Ci [256, 512). K chunk = 64 bytes per row (32 bf16 / 16 fp32), 64B swizzle,
+// two pipeline stages of 96 KB.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+
+#include "tevo_tc.h"
+
+namespace tevo {
+
+namespace {
+
+constexpr int TM = 128, TN = 256;
+constexpr int KCB = 64;  // bytes of K per stage row
+constexpr int NSTAGE = 2;
+constexpr int A_BYTES = 4 * TM * KCB;  // 32 KB (4 planes max)
+constexpr int B_BYTES = 4 * TN * KCB;  // 64 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int TC_THREADS = 192;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // bounded waits: 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// wait on an mbarrier phase with a time limit; false (and the error flag set)
+// when the limit passes
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (gtimer() - t0 > WAIT_NS) {
+      atomicExch(err, code);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 64B swizzle, 8-row groups 512 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;         // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)1 << 46;                  // descriptor version for tcgen05
+  d |= (uint64_t)4 << 61;                  // swizzle mode: 64B
+  return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  if constexpr (KIND == TC_BF16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// write one complex value into the planes of an output map
+__device__ __forceinline__ void put(const TcOutMap& o, int fmt, long long off, float re, float im) {
+  if (fmt == TC_BF16) {
+    __nv_bfloat16* p = reinterpret_cast<__nv_bfloat16*>(o.base) + off;
+    __nv_bfloat16 rh = __float2bfloat16_rn(re), ih = __float2bfloat16_rn(im);
+    p[0] = rh;
+    p[o.plane_stride] = __float2bfloat16_rn(re - __bfloat162float(rh));
+    p[2 * o.plane_stride] = ih;
+    p[3 * o.plane_stride] = __float2bfloat16_rn(im - __bfloat162float(ih));
+  } else if (fmt == TC_TF32X3) {
+    float* p = reinterpret_cast<float*>(o.base) + off;
+    float rh = tf32_round(re), ih = tf32_round(im);
+    p[0] = rh;
+    p[o.plane_stride] = tf32_round(re - rh);
+    p[2 * o.plane_stride] = ih;
+    p[3 * o.plane_stride] = tf32_round(im - ih);
+  } else {
+    float* p = reinterpret_cast<float*>(o.base) + off;
+    p[0] = tf32_round(re);
+    p[o.plane_stride] = tf32_round(im);
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSTAGE + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSTAGE), accb = smem_u32(bars + 2 * NSTAGE);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int kt0 = blockIdx.z * a.tiles_per_split;
+  const int kt1 = min(a.k_tiles, kt0 + a.tiles_per_split);
+  const int nk = kt1 > kt0 ? kt1 - kt0 : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int planes = a.planes;
+  const uint32_t bytesA = planes * TM * KCB, bytesB = planes * TN * KCB;
+
+  if (warp == 0) {
+    if (lane == 0 && nk > 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      const int kc_elems = KCB / a.elem_bytes;
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % NSTAGE;
+        const uint32_t ph = (i / NSTAGE) & 1;
+        if (!mbar_wait(empty0 + 8 * s, ph ^ 1, a.err, 1)) break;
+        const uint32_t fb = full0 + 8 * s;
+        mbar_expect_tx(fb, bytesA + bytesB);
+        const int kt = kt0 + i;
+        const int ko = kt / a.k_in_chunks, kc = (kt % a.k_in_chunks) * kc_elems;
+        uint8_t* st = smem + s * STAGE_BYTES;
+        tma_load_4d(smem_u32(st), &tmA, kc, ko, m0, 0, fb);
+        tma_load_4d(smem_u32(st + A_BYTES), &tmB, kc, ko, n0, 0, fb);
+        issued = i + 1;
+      }
+      // do not leave while copies are in flight: wait for the stages just filled
+      for (int i = (issued > NSTAGE ? issued - NSTAGE : 0); i < issued; ++i)
+        mbar_wait(full0 + 8 * (i % NSTAGE), (i / NSTAGE) & 1, a.err, 2);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && nk > 0) {
+      // instruction descriptor: fp32 accumulate, K-major A and B, M = 128, N = 256
+      const uint32_t fmtAB = (KIND == TC_BF16) ? 1u : 2u;
+      const uint32_t base_id = (1u << 4) | (fmtAB << 7) | (fmtAB << 10) | ((uint32_t)(TN >> 3) << 17) |
+                               ((uint32_t)(TM >> 4) << 24);
+      bool started[2] = {false, false};
+      bool ok = true;
+      for (int i = 0; i < nk && ok; ++i) {
+        const int s = i % NSTAGE;
+        const uint32_t ph = (i / NSTAGE) & 1;
+        if (!mbar_wait(full0 + 8 * s, ph, a.err, 3)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
+#pragma unroll
+        for (int ks = 0; ks < KCB / 32; ++ks) {
+          for (int p = 0; p < a.nprod; ++p) {
+            const uint64_t ad = sdesc(sa + a.a_plane[p] * TM * KCB + ks * 32);
+            const uint64_t bd = sdesc(sb + a.b_plane[p] * TN * KCB + ks * 32);
+            const int acc = a.acc[p];
+            const uint32_t id = base_id | (a.neg[p] ? (1u << 13) : 0u);
+            mma<KIND>(tmem + acc * TN, ad, bd, id, started[acc] ? 1u : 0u);
+            started[acc] = true;
+          }
+        }
+        mma_commit(empty0 + 8 * s);
+      }
+      mma_commit(accb);
+    }
+  } else {
+    // epilogue: warps 2..5 own tensor-memory lane quarters (warp % 4)
+    const int q = warp % 4;
+    const int m = m0 + q * 32 + lane;
+    bool ok = true;
+    if (nk > 0) ok = mbar_wait(accb, 0, a.err, 4);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        uint32_t rr[32], ri[32];
+        if (nk > 0) {
+          tmem_ld32(trow + c0, rr);
+          tmem_ld32(trow + TN + c0, ri);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) rr[j] = ri[j] = 0u;
+        }
+        if (m >= a.M) continue;
+        if (a.out_mode == TC_OUT_PARTIAL) {
+          float2* P = a.partial + ((long long)blockIdx.z * a.M + m) * (long long)a.N;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = n0 + c0 + j;
+            if (n < a.N) P[n] = make_float2(__uint_as_float(rr[j]), __uint_as_float(ri[j]));
+          }
+        } else {
+          for (int o = 0; o < a.nout; ++o) {
+            const TcOutMap& om = a.out[o];
+            const long long mo = (long long)(m / om.M2) * om.sM1 + (long long)(m % om.M2) * om.sM2;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int n = n0 + c0 + j;
+              if (n < a.N) {
+                const long long off = mo + (long long)(n / om.N2) * om.sN1 + (long long)(n % om.N2) * om.sN2;
+                put(om, a.fmt, off, __uint_as_float(rr[j]), __uint_as_float(ri[j]));
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// fp64 (or fp32 partial) source -> planes, with two-level index maps
+__global__ void to_planes_kernel(TcConvert c) {
+  const long long total = (long long)c.rows * c.K;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = int(idx / c.K), k = int(idx % c.K);
+    const long long so = (long long)(r / c.R2) * c.sR1 + (long long)(r % c.R2) * c.sR2 +
+                         (long long)(k / c.K2) * c.sK1 + (long long)(k % c.K2) * c.sK2;
+    double2 v = reinterpret_cast<const double2*>(c.src)[so];
+    if (c.conj) v.y = -v.y;
+    const long long doff = (long long)r * c.row_pitch + (long long)(k / c.kin) * c.kout_pitch + (k % c.kin);
+    put(c.dst, c.fmt, doff, float(v.x), float(v.y));
+  }
+}
+
+// sum split-K partials (fixed order) into fp64 with a strided store
+__global__ void reduce_partials_kernel(const float2* P, int splits, int M, int N, double2* out, long long sm,
+                                       long long sn) {
+  const long long total = (long long)M * N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int m = int(idx / N), n = int(idx % N);
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < splits; ++s) {
+      float2 v = P[((long long)s * M + m) * N + n];
+      re += v.x;
+      im += v.y;
+    }
+    out[m * sm + n * sn] = make_double2(re, im);
+  }
+}
+
+__global__ void fill_planes_kernel(TcOutMap o, int fmt, long long n) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    put(o, fmt, idx, 0.f, 0.f);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+int make_map(CUtensorMap* m, const TcOperand& o, int tile_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return TEVO_ECUDA;
+  const int eb = o.elem_bytes;
+  if ((reinterpret_cast<uintptr_t>(o.base) & 15) || ((o.row_pitch * eb) & 15) || ((o.kout_pitch * eb) & 15) ||
+      ((o.plane_stride * eb) & 15))
+    return TEVO_ESHAPE;
+  cuuint64_t dims[4] = {(cuuint64_t)o.k_in, (cuuint64_t)o.k_out, (cuuint64_t)o.rows, (cuuint64_t)o.planes};
+  cuuint64_t strides[3] = {(cuuint64_t)(o.k_out > 1 ? o.kout_pitch : o.row_pitch) * eb,
+                           (cuuint64_t)o.row_pitch * eb, (cuuint64_t)o.plane_stride * eb};
+  cuuint32_t box[4] = {(cuuint32_t)(KCB / eb), 1u, (cuuint32_t)tile_rows, (cuuint32_t)o.planes};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, eb == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                   const_cast<void*>(o.base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : TEVO_ESHAPE;
+}
+
+int grid_for(long long n, int sms) {
+  long long b = (n + 255) / 256;
+  if (b > 16LL * sms) b = 16LL * sms;
+  return int(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int tc_planes(int fmt) { return fmt == TC_TF32 ? 2 : 4; }
+int tc_elem_bytes(int fmt) { return fmt == TC_BF16 ? 2 : 4; }
+int tc_kchunk(int fmt) { return KCB / tc_elem_bytes(fmt); }
+
+void tc_products(int fmt, TcArgs& a) {
+  if (fmt == TC_TF32) {
+    // planes: 0 re, 1 im
+    const int8_t ap[4] = {0, 1, 0, 1}, bp[4] = {0, 1, 1, 0}, ac[4] = {0, 0, 1, 1}, ng[4] = {0, 1, 0, 0};
+    a.nprod = 4;
+    for (int i = 0; i < 4; ++i) {
+      a.a_plane[i] = ap[i];
+      a.b_plane[i] = bp[i];
+      a.acc[i] = ac[i];
+      a.neg[i] = ng[i];
+    }
+  } else {
+    // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo; hi.hi + hi.lo + lo.hi per real product
+    const int8_t ap[12] = {0, 0, 1, 2, 2, 3, 0, 0, 1, 2, 2, 3};
+    const int8_t bp[12] = {0, 1, 0, 2, 3, 2, 2, 3, 2, 0, 1, 0};
+    const int8_t ac[12] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1};
+    const int8_t ng[12] = {0, 0, 0, 1, 1, 1, 0, 0, 0, 0, 0, 0};
+    a.nprod = 12;
+    for (int i = 0; i < 12; ++i) {
+      a.a_plane[i] = ap[i];
+      a.b_plane[i] = bp[i];
+      a.acc[i] = ac[i];
+      a.neg[i] = ng[i];
+    }
+  }
+}
+
+int tc_gemm(const Launch& L, int fmt, const TcOperand& A, const TcOperand& B, int M, int N, TcArgs args) {
+  static bool attr_done[2] = {false, false};
+  const int kind = fmt == TC_BF16 ? 0 : 1;
+  if (!attr_done[kind]) {
+    cudaError_t e = kind == 0 ? cudaFuncSetAttribute(tc_gemm_kernel<TC_BF16>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
+                              : cudaFuncSetAttribute(tc_gemm_kernel<TC_TF32>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return TEVO_ECUDA;
+    attr_done[kind] = true;
+  }
+  if (A.k_in != B.k_in || A.k_out != B.k_out || A.planes != B.planes || A.elem_bytes != B.elem_bytes)
+    return TEVO_ESHAPE;
+  if (A.rows < M || B.rows < N) return TEVO_ESHAPE;
+  CUtensorMap ma, mb;
+  int e = make_map(&ma, A, TM);
+  if (!e) e = make_map(&mb, B, TN);
+  if (e) return e;
+  args.M = M;
+  args.N = N;
+  args.planes = A.planes;
+  args.elem_bytes = A.elem_bytes;
+  args.fmt = fmt;
+  const int kc = KCB / A.elem_bytes;
+  args.k_in_chunks = (A.k_in + kc - 1) / kc;
+  args.k_tiles = args.k_in_chunks * A.k_out;
+  int splits = args.splits < 1 ? 1 : args.splits;
+  if (args.out_mode != TC_OUT_PARTIAL) splits = 1;
+  args.tiles_per_split = (args.k_tiles + splits - 1) / splits;
+  splits = (args.k_tiles + args.tiles_per_split - 1) / args.tiles_per_split;
+  args.splits = splits;
+  tc_products(fmt, args);
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, splits);
+  if (grid.y > 65535 || grid.z > 65535) return TEVO_ESHAPE;
+  const double useful = 8.0 * (double)M * N * (double)A.k_in * A.k_out;
+  int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_GEMMTC, useful,
+                                  (double)A.elem_bytes * A.planes * ((double)M + N) * A.k_in * A.k_out)
+                  : -1;
+  if (kind == 0)
+    tc_gemm_kernel<TC_BF16><<<grid, TC_THREADS, SMEM_BYTES, L.stream>>>(ma, mb, args);
+  else
+    tc_gemm_kernel<TC_TF32><<<grid, TC_THREADS, SMEM_BYTES, L.stream>>>(ma, mb, args);
+  ++*L.launches;
+  if (L.prof) L.prof->end(L.stream, pr);
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int tc_to_planes(const Launch& L, const TcConvert& c) {
+  const long long total = (long long)c.rows * c.K;
+  if (total <= 0) return 0;
+  to_planes_kernel<<<grid_for(total, L.num_sms), 256, 0, L.stream>>>(c);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int tc_reduce_partials(const Launch& L, const float2* P, int splits, int M, int N, void* out, long long sm,
+                       long long sn) {
+  const long long total = (long long)M * N;
+  reduce_partials_kernel<<<grid_for(total, L.num_sms), 256, 0, L.stream>>>(P, splits, M, N,
+                                                                           reinterpret_cast<double2*>(out), sm, sn);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int tc_zero_planes(const Launch& L, const TcOutMap& o, int fmt, long long n) {
+  if (n <= 0) return 0;
+  fill_planes_kernel<<<grid_for(n, L.num_sms), 256, 0, L.stream>>>(o, fmt, n);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+}  // namespace tevo

@@ -17,6 +17,12 @@ int mixed_prepare(tevo_ctx c, tevo_mpo W, tevo_mps s, int precision);
 int mixed_build_right_envs(tevo_ctx c, tevo_mpo W, tevo_mps s, bool bra_fresh, int precision);
 // one sweep with tensor-core contractions and fp64 QR
 int mixed_sweep(tevo_ctx c, tevo_mpo W, tevo_mps s, int precision);
+// centre at site 1 with tensor-core contractions (into the fitted set)
+int mixed_centre(tevo_ctx c, tevo_mpo W, tevo_mps s, int precision);
+// device error flag of the tensor-core kernels (bounded waits); copies it to *flag (async)
+int mixed_error_flag(tevo_ctx c, tevo_mps s, int* flag);
+// standalone complex GEMM (tevo_gemm)
+int mixed_gemm(tevo_ctx c, int precision, int M, int N, int K, const void* A, const void* B, void* C);
 void mixed_mpo_destroy(tevo_ctx c, MixedMPO*& m);
 void mixed_state_destroy(tevo_ctx c, MixedState*& m);
 
