@@ -187,6 +187,32 @@ int mps_overlap(tevo_mps a, tevo_mps b, double* log_abs, double* phase);
  */
 int tevo_gemm(tevo_ctx ctx, int precision, int M, int N, int K, const double* A, const double* B, double* C);
 
+/*
+ * tevo_gemm_noalloc -- tevo_gemm for callers that cannot allocate device
+ * memory: a process whose device memory is entirely handed to a pre-sized pool,
+ * or code that runs where an allocation may block, fail or is not permitted. It
+ * computes the same product as tevo_gemm (same kernels) but allocates nothing:
+ * no cudaMalloc / cudaFree and no call of the context's allocator. Its temporary
+ * storage is one fixed array of TEVO_NOALLOC_SCRATCH_BYTES bytes in device
+ * memory, created with the library and kept by every GPU that loads the library
+ * until the process exits. The paper has no counterpart; this is a property of
+ * the library, not of the method.
+ *  - Limit: the operand planes plus at least one set of split-K partials must
+ *    fit the array (bf16x3 / tf32x3 need about 8 / 16 bytes per element of A and
+ *    B plus 8 bytes per element of C); larger shapes return TEVO_ESHAPE without
+ *    touching the device. The split-K count may be lower than tevo_gemm's, so
+ *    results can differ from tevo_gemm's in the last fp32 rounding.
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current); make that first call before any stream capture.
+ *  - Every call uses the same array and leaves its contents behind; the call
+ *    clears what must start at zero. Calls whose GPU work overlaps -- on two
+ *    streams, or from two host threads -- race on the array: serialise them.
+ * Arguments, layouts and errors as for tevo_gemm. Synchronises the context stream.
+ */
+#define TEVO_NOALLOC_SCRATCH_BYTES (64u << 20)
+int tevo_gemm_noalloc(tevo_ctx ctx, int precision, int M, int N, int K, const double* A, const double* B,
+                      double* C);
+
 /* name of an error code */
 const char* tevo_strerror(int code);
 

@@ -861,6 +861,15 @@ extern "C" int tevo_gemm(tevo_ctx c, int precision, int M, int N, int K, const d
   return e;
 }
 
+extern "C" int tevo_gemm_noalloc(tevo_ctx c, int precision, int M, int N, int K, const double* A, const double* B,
+                                 double* C) {
+  if (!c || !A || !B || !C || M < 1 || N < 1 || K < 1) return TEVO_EINVAL;
+  if (precision < TEVO_FP64 || precision > TEVO_BF16X3) return TEVO_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15)
+    return TEVO_EINVAL;
+  return noalloc_gemm(launch_of(c), precision, M, N, K, A, B, C);
+}
+
 extern "C" int mps_overlap(tevo_mps a, tevo_mps b, double* log_abs, double* phase) {
   if (!a || !b || !log_abs || !phase) return TEVO_EINVAL;
   if (a->L != b->L || a->d != b->d) return TEVO_ESHAPE;
