@@ -159,6 +159,21 @@ int evolve_step(tevo_mps psi, tevo_mpo W, double tau_re, double tau_im, int D, i
                 int precision);
 
 /*
+ * evolve_step_batched -- one time step of n independent chains (each with its
+ * own MPO, using that MPO's tau and each state's own D), the batched form of
+ * evolve_step. Same sweeps / precision for every chain; each chain's result is
+ * exactly the one evolve_step would give it.
+ * The chains run concurrently on internal worker streams forked from the first
+ * state's context stream and joined back into it. The first calls are issued
+ * directly and time three schedules (worker-stream counts, largest chain first);
+ * once every chain is in right-canonical form and the schedule is chosen, a
+ * step is captured into a CUDA graph (one per psi/phi buffer parity) and later
+ * steps replay it. Handles must not be used from other streams meanwhile.
+ * Errors: as evolve_step, for the first failing chain. Synchronises.
+ */
+int evolve_step_batched(tevo_mps* psis, const tevo_mpo* Ws, int n, int sweeps, int precision);
+
+/*
  * measure_local -- <O_i> = <psi|O_i|psi>/<psi|psi> for every site i and each of
  * nops single-site operators (the local observables of Sec. 7.2), in any gauge.
  * ops: complex [nops][d][d] host; out: complex [nops][L] host.

@@ -24,7 +24,7 @@ from ._lib import (FP64, TF32, TF32X3, BF16X3, TC_ONLY, MPO_PLAIN, MPO_EXACT, MP
                    TevoError)
 
 __all__ = [
-    "Context", "MPO", "MPS", "mpo_build", "mpo_build_host", "mps_init", "evolve_step", "measure_local", "mps_overlap",
+    "Context", "MPO", "MPS", "mpo_build", "mpo_build_host", "mps_init", "evolve_step", "evolve_step_batched", "measure_local", "mps_overlap",
     "FP64", "TF32", "TF32X3", "BF16X3", "TC_ONLY", "MPO_PLAIN", "MPO_EXACT", "MPO_EXTENDED", "MPO_FULL",
     "TevoError", "library_path",
 ]
@@ -236,6 +236,16 @@ def evolve_step(psi, W, tau, D, sweeps=1, precision=FP64):
     tau = complex(tau)
     _lib.check(_lib.lib.evolve_step(psi.handle, W.handle, tau.real, tau.imag, int(D), int(sweeps),
                                     int(precision)))
+
+
+def evolve_step_batched(psis, Ws, sweeps=1, precision=FP64):
+    """One time step of independent chains (each with its own MPO and its MPO's tau)."""
+    n = len(psis)
+    if n != len(Ws) or n == 0:
+        raise ValueError("need one MPO per state")
+    ps = (_lib.tevo_mps * n)(*[p.handle for p in psis])
+    ws = (_lib.tevo_mpo * n)(*[w.handle for w in Ws])
+    _lib.check(_lib.lib.evolve_step_batched(ps, ws, n, int(sweeps), int(precision)))
 
 
 def measure_local(psi, ops):

@@ -58,6 +58,7 @@ _SIGS = {
     "mps_log_norm": [tevo_mps, _pd],
     "mps_destroy": [tevo_mps],
     "evolve_step": [tevo_mps, tevo_mpo, _d, _d, _i, _i, _i],
+    "evolve_step_batched": [ctypes.POINTER(tevo_mps), ctypes.POINTER(tevo_mpo), _i, _i, _i],
     "measure_local": [tevo_mps, _i, _pd, _pd],
     "mps_overlap": [tevo_mps, tevo_mps, _pd, _pd],
     "tevo_gemm": [tevo_ctx, _i, _i, _i, _i, _p, _p, _p],

@@ -31,6 +31,10 @@
 
 using namespace tevo;
 
+namespace tevo {
+long long g_persist_gen = 0;
+}
+
 struct tevo_ctx_s {
   cudaStream_t stream = nullptr;
   tevo_alloc_fn alloc = nullptr;
@@ -83,6 +87,7 @@ void dfree(tevo_ctx c, Buf& b) {
 
 int ensure(tevo_ctx c, Buf& b, size_t bytes) {
   if (b.bytes >= bytes && b.p) return 0;
+  ++g_persist_gen;
   dfree(c, b);
   return dalloc(c, b, bytes);
 }
@@ -109,6 +114,7 @@ struct tevo_mps_s {
   std::vector<int> dims;
   std::vector<Buf> A, Anew;
   bool canonical = false;
+  int parity = 0;  // flips with every psi/phi swap
   Buf scalars;  // [0] lognorm, [1] nrm2, [2] overlap log acc, [3..] flags/values
   // workspace of evolve_step
   std::vector<size_t> env_off;
@@ -215,6 +221,7 @@ int workspace(tevo_mps s, tevo_mpo W) {
   int wmax = 1;
   for (int i = 0; i < L; ++i) wmax = std::max({wmax, W->wl[i], W->wr[i]});
   if (s->env.p && s->wmax >= wmax) return 0;
+  ++g_persist_gen;
   s->wmax = wmax;
   s->env_off.assign(L + 1, 0);
   size_t off = 0;
@@ -330,6 +337,7 @@ int finish_step(tevo_mps s) {
   TRY(norm2_64(L, zp(s->Anew[0]), n0, scal(s, 1), static_cast<double*>(s->red.p)));
   TRY(normalize64(L, zp(s->Anew[0]), n0, scal(s, 1), scal(s, 0), reinterpret_cast<int*>(scal(s, 4))));
   std::swap(s->A, s->Anew);
+  s->parity ^= 1;
   s->canonical = true;
   return 0;
 }
@@ -668,15 +676,23 @@ extern "C" int mps_destroy(tevo_mps s) {
 // ---------------------------------------------------------------------------
 // evolve_step
 // ---------------------------------------------------------------------------
-extern "C" int evolve_step(tevo_mps s, tevo_mpo W, double tau_re, double tau_im, int D, int sweeps, int precision) {
+namespace {
+
+int check_step_args(tevo_mps s, tevo_mpo W, int sweeps, int precision) {
   if (!s || !W || sweeps < 1) return TEVO_EINVAL;
   const bool tc_only = (precision & TEVO_TC_ONLY) != 0;
   precision &= ~TEVO_TC_ONLY;
   if (precision < TEVO_FP64 || precision > TEVO_BF16X3) return TEVO_EINVAL;
   if (tc_only && precision == TEVO_FP64) return TEVO_EINVAL;
   if (W->L != s->L || W->d != s->d) return TEVO_ESHAPE;
-  if (D != s->D) return TEVO_ESHAPE;
-  if (tau_re != W->tau_re || tau_im != W->tau_im) return TEVO_ETAU;
+  return 0;
+}
+
+// issue one time step on the context stream; no host synchronisation (so it can
+// be captured in a CUDA graph once the workspaces exist)
+int evolve_issue(tevo_mps s, tevo_mpo W, int sweeps, int precision, bool* mixed_out) {
+  const bool tc_only = (precision & TEVO_TC_ONLY) != 0;
+  precision &= ~TEVO_TC_ONLY;
   tevo_ctx c = s->ctx;
   TRY(workspace(s, W));
   Launch L = launch_of(c);
@@ -714,13 +730,237 @@ extern "C" int evolve_step(tevo_mps s, tevo_mpo W, double tau_re, double tau_im,
     TRY(centre64(s, W));
   }
   TRY(finish_step(s));
+  *mixed_out = mixed;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+// device flags of the step just issued (synchronises the context stream)
+int evolve_check(tevo_mps s, bool mixed) {
+  tevo_ctx c = s->ctx;
   int flag = 0, tflag = 0;
   TRYCUDA(cudaMemcpyAsync(&flag, scal(s, 4), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   if (mixed) TRY(mixed_error_flag(c, s, &tflag));
   TRYCUDA(cudaStreamSynchronize(c->stream));
   if (tflag) return TEVO_ETIMEOUT;
   if (flag) return TEVO_ENONFINITE;
-  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" int evolve_step(tevo_mps s, tevo_mpo W, double tau_re, double tau_im, int D, int sweeps, int precision) {
+  TRY(check_step_args(s, W, sweeps, precision));
+  if (D != s->D) return TEVO_ESHAPE;
+  if (tau_re != W->tau_re || tau_im != W->tau_im) return TEVO_ETAU;
+  bool mixed = false;
+  TRY(evolve_issue(s, W, sweeps, precision, &mixed));
+  return evolve_check(s, mixed);
+}
+
+// ---------------------------------------------------------------------------
+// batched form: independent chains stepped together
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchPlan {
+  std::vector<tevo_mps> psis;
+  std::vector<tevo_mpo> Ws;
+  int sweeps = 0, precision = 0;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t origin = nullptr;  // stream the graph is captured on and launched from
+  std::vector<int> order;         // issue order of the chains
+  int nstreams = 0;
+  int tune_next = 0;              // index into the candidate list while tuning
+  std::vector<std::pair<int, float>> tuned;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  long long graph_launches[2] = {0, 0};
+  long long gen[2] = {-1, -1};  // g_persist_gen at capture
+  bool mixed = false;
+};
+
+BatchPlan* g_plan_cache = nullptr;  // one plan per process (the last batch used)
+
+void plan_free(BatchPlan* p) {
+  if (!p) return;
+  for (auto& e : p->exec)
+    if (e) cudaGraphExecDestroy(e);
+  for (auto& st : p->streams) cudaStreamDestroy(st);
+  for (auto& ev : p->done) cudaEventDestroy(ev);
+  if (p->fork) cudaEventDestroy(p->fork);
+  if (p->origin) cudaStreamDestroy(p->origin);
+  delete p;
+}
+
+// work of one chain step (useful MACs), for the largest-first issue order
+double chain_work(tevo_mps s, tevo_mpo W) {
+  double w = 0;
+  for (int i = 0; i < s->L; ++i)
+    w += (double)s->dims[i] * s->dims[i + 1] * (s->dims[i] + s->dims[i + 1]) * W->wr[i];
+  return w;
+}
+
+int plan_streams(BatchPlan* p, int nstreams) {
+  while ((int)p->streams.size() < nstreams) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    TRYCUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    TRYCUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    p->streams.push_back(st);
+    p->done.push_back(ev);
+  }
+  p->nstreams = nstreams;
+  return 0;
+}
+
+// issue every chain's step on the worker streams, forked from and joined into origin
+int batch_issue(BatchPlan* p, cudaStream_t origin) {
+  TRYCUDA(cudaEventRecord(p->fork, origin));
+  for (int k = 0; k < p->nstreams; ++k) TRYCUDA(cudaStreamWaitEvent(p->streams[k], p->fork, 0));
+  for (size_t j = 0; j < p->order.size(); ++j) {
+    const int c = p->order[j];
+    tevo_mps s = p->psis[c];
+    cudaStream_t saved = s->ctx->stream;
+    s->ctx->stream = p->streams[j % p->nstreams];
+    bool mixed = false;
+    int e = evolve_issue(s, p->Ws[c], p->sweeps, p->precision, &mixed);
+    s->ctx->stream = saved;
+    if (e) return e;
+    p->mixed = mixed;
+  }
+  for (int k = 0; k < p->nstreams; ++k) {
+    TRYCUDA(cudaEventRecord(p->done[k], p->streams[k]));
+    TRYCUDA(cudaStreamWaitEvent(origin, p->done[k], 0));
+  }
+  return 0;
+}
+
+int batch_check(BatchPlan* p) {
+  for (size_t c = 0; c < p->psis.size(); ++c) {
+    tevo_mps s = p->psis[c];
+    int flag = 0, tflag = 0;
+    TRYCUDA(cudaMemcpy(&flag, scal(s, 4), sizeof(int), cudaMemcpyDeviceToHost));
+    if (p->mixed) {
+      TRY(mixed_error_flag(s->ctx, s, &tflag));
+      TRYCUDA(cudaStreamSynchronize(s->ctx->stream));
+    }
+    if (tflag) return TEVO_ETIMEOUT;
+    if (flag) return TEVO_ENONFINITE;
+  }
+  return 0;
+}
+
+}  // namespace
+
+extern "C" int evolve_step_batched(tevo_mps* psis, const tevo_mpo* Ws, int n, int sweeps, int precision) {
+  if (!psis || !Ws || n < 1) return TEVO_EINVAL;
+  for (int c = 0; c < n; ++c) TRY(check_step_args(psis[c], Ws[c], sweeps, precision));
+  for (int c = 0; c < n; ++c)
+    for (int k = c + 1; k < n; ++k)
+      if (psis[c] == psis[k]) return TEVO_EINVAL;
+  tevo_ctx c0 = psis[0]->ctx;
+  // reuse the cached plan when the batch is the same
+  BatchPlan* p = g_plan_cache;
+  bool same = p && p->sweeps == sweeps && p->precision == precision && (int)p->psis.size() == n;
+  for (int c = 0; same && c < n; ++c) same = p->psis[c] == psis[c] && p->Ws[c] == Ws[c];
+  if (!same) {
+    plan_free(g_plan_cache);
+    g_plan_cache = p = new BatchPlan;
+    p->psis.assign(psis, psis + n);
+    p->Ws.assign(Ws, Ws + n);
+    p->sweeps = sweeps;
+    p->precision = precision;
+    TRYCUDA(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+    TRYCUDA(cudaStreamCreateWithFlags(&p->origin, cudaStreamNonBlocking));
+    p->order.resize(n);
+    std::vector<double> work(n);
+    for (int c = 0; c < n; ++c) {
+      p->order[c] = c;
+      work[c] = chain_work(psis[c], Ws[c]);
+    }
+    // largest chains first, so the longest dependency chains start earliest
+    std::stable_sort(p->order.begin(), p->order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  }
+  bool all_canonical = true;
+  for (int c = 0; c < n; ++c) all_canonical = all_canonical && psis[c]->canonical;
+  // the caller's stream orders the batch against its other work
+  cudaStream_t caller = c0->stream;
+  TRYCUDA(cudaEventRecord(p->fork, caller));
+  TRYCUDA(cudaStreamWaitEvent(p->origin, p->fork, 0));
+  // candidate schedules: worker-stream counts, tried once each (uncaptured, timed)
+  const int cands[3] = {std::min(n, 64), std::min(n, 16), std::min(n, 4)};
+  if (!all_canonical || p->tune_next < 3) {
+    const int k = all_canonical ? p->tune_next : 0;
+    TRY(plan_streams(p, cands[k]));
+    cudaEvent_t t0, t1;
+    TRYCUDA(cudaEventCreate(&t0));
+    TRYCUDA(cudaEventCreate(&t1));
+    TRYCUDA(cudaEventRecord(t0, p->origin));
+    TRY(batch_issue(p, p->origin));
+    TRYCUDA(cudaEventRecord(t1, p->origin));
+    TRYCUDA(cudaEventSynchronize(t1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, t0, t1);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (all_canonical) {
+      p->tuned.push_back({cands[k], ms});
+      ++p->tune_next;
+      if (p->tune_next == 3) {
+        int best = p->tuned[0].first;
+        float bms = p->tuned[0].second;
+        for (auto& t : p->tuned)
+          if (t.second < bms) {
+            best = t.first;
+            bms = t.second;
+          }
+        TRY(plan_streams(p, best));
+      }
+    }
+  } else {
+    // a captured step reads and writes the buffers of the parity it was captured at
+    int par = psis[0]->parity;
+    bool common = true;
+    for (int c = 1; c < n; ++c) common = common && psis[c]->parity == par;
+    for (int q = 0; q < 2; ++q)
+      if (p->exec[q] && p->gen[q] != g_persist_gen) {
+        cudaGraphExecDestroy(p->exec[q]);
+        p->exec[q] = nullptr;
+      }
+    if (!common || c0->prof.on) {
+      TRY(batch_issue(p, p->origin));
+    } else if (!p->exec[par]) {
+      cudaGraph_t g;
+      const long long before = c0->launches;
+      TRYCUDA(cudaStreamBeginCapture(p->origin, cudaStreamCaptureModeThreadLocal));
+      int e = batch_issue(p, p->origin);  // swaps every chain's psi/phi (host side)
+      cudaError_t ce = cudaStreamEndCapture(p->origin, &g);
+      if (e) return e;
+      if (ce != cudaSuccess) return TEVO_ECUDA;
+      cudaError_t ie = cudaGraphInstantiate(&p->exec[par], g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        p->exec[par] = nullptr;
+        return TEVO_ECUDA;
+      }
+      p->graph_launches[par] = c0->launches - before;
+      p->gen[par] = g_persist_gen;
+      TRYCUDA(cudaGraphLaunch(p->exec[par], p->origin));
+    } else {
+      // replay, repeating the host-side psi/phi swap of every chain
+      for (int c = 0; c < n; ++c) {
+        std::swap(psis[c]->A, psis[c]->Anew);
+        psis[c]->parity ^= 1;
+      }
+      TRYCUDA(cudaGraphLaunch(p->exec[par], p->origin));
+      c0->launches += p->graph_launches[par];
+    }
+  }
+  TRYCUDA(cudaEventRecord(p->fork, p->origin));
+  TRYCUDA(cudaStreamWaitEvent(caller, p->fork, 0));
+  TRYCUDA(cudaStreamSynchronize(caller));
+  return batch_check(p);
 }
 
 // accessors used by the mixed-precision translation unit

@@ -167,6 +167,92 @@ __device__ __forceinline__ void put(const TcOutMap& o, int fmt, long long off, f
   }
 }
 
+// 32 consecutive complex values of one row into every plane with 16-byte stores
+__device__ __forceinline__ void put_row32(const TcOutMap& o, int fmt, long long off, const uint32_t* rr,
+                                          const uint32_t* ri) {
+  if (fmt == TC_BF16) {
+    uint32_t h[4][16];
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) {
+      float r0 = __uint_as_float(rr[j]), r1 = __uint_as_float(rr[j + 1]);
+      float i0 = __uint_as_float(ri[j]), i1 = __uint_as_float(ri[j + 1]);
+      __nv_bfloat16 rh0 = __float2bfloat16_rn(r0), rh1 = __float2bfloat16_rn(r1);
+      __nv_bfloat16 ih0 = __float2bfloat16_rn(i0), ih1 = __float2bfloat16_rn(i1);
+      __nv_bfloat16 rl0 = __float2bfloat16_rn(r0 - __bfloat162float(rh0));
+      __nv_bfloat16 rl1 = __float2bfloat16_rn(r1 - __bfloat162float(rh1));
+      __nv_bfloat16 il0 = __float2bfloat16_rn(i0 - __bfloat162float(ih0));
+      __nv_bfloat16 il1 = __float2bfloat16_rn(i1 - __bfloat162float(ih1));
+      h[0][j / 2] = (uint32_t)__bfloat16_as_ushort(rh0) | ((uint32_t)__bfloat16_as_ushort(rh1) << 16);
+      h[1][j / 2] = (uint32_t)__bfloat16_as_ushort(rl0) | ((uint32_t)__bfloat16_as_ushort(rl1) << 16);
+      h[2][j / 2] = (uint32_t)__bfloat16_as_ushort(ih0) | ((uint32_t)__bfloat16_as_ushort(ih1) << 16);
+      h[3][j / 2] = (uint32_t)__bfloat16_as_ushort(il0) | ((uint32_t)__bfloat16_as_ushort(il1) << 16);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(o.base) + off + p * o.plane_stride);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = make_uint4(h[p][4 * q], h[p][4 * q + 1], h[p][4 * q + 2], h[p][4 * q + 3]);
+    }
+  } else if (fmt == TC_TF32X3) {
+    float* base = reinterpret_cast<float*>(o.base) + off;
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+      float4 a0, a1, a2, a3;
+      float* v0 = &a0.x;
+      float* v1 = &a1.x;
+      float* v2 = &a2.x;
+      float* v3 = &a3.x;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float r = __uint_as_float(rr[j + t]), im = __uint_as_float(ri[j + t]);
+        float rh = tf32_round(r), ih = tf32_round(im);
+        v0[t] = rh;
+        v1[t] = tf32_round(r - rh);
+        v2[t] = ih;
+        v3[t] = tf32_round(im - ih);
+      }
+      *reinterpret_cast<float4*>(base + j) = a0;
+      *reinterpret_cast<float4*>(base + o.plane_stride + j) = a1;
+      *reinterpret_cast<float4*>(base + 2 * o.plane_stride + j) = a2;
+      *reinterpret_cast<float4*>(base + 3 * o.plane_stride + j) = a3;
+    }
+  } else {
+    float* base = reinterpret_cast<float*>(o.base) + off;
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+      *reinterpret_cast<float4*>(base + j) =
+          make_float4(tf32_round(__uint_as_float(rr[j])), tf32_round(__uint_as_float(rr[j + 1])),
+                      tf32_round(__uint_as_float(rr[j + 2])), tf32_round(__uint_as_float(rr[j + 3])));
+      *reinterpret_cast<float4*>(base + o.plane_stride + j) =
+          make_float4(tf32_round(__uint_as_float(ri[j])), tf32_round(__uint_as_float(ri[j + 1])),
+                      tf32_round(__uint_as_float(ri[j + 2])), tf32_round(__uint_as_float(ri[j + 3])));
+    }
+  }
+}
+
+// batched transpose of plane-format matrices: dst(c, r) <- src(r, c), tile 32 x 32
+template <typename T>
+__global__ void transpose_planes_kernel(TcTranspose t) {
+  __shared__ T tile[32][33];
+  const int nb = t.batch;
+  const int z = blockIdx.z;
+  const int plane = z / nb, b = z % nb;
+  const T* src = reinterpret_cast<const T*>(t.src) + plane * t.src_plane + (long long)(b / t.B2) * t.sb1 +
+                 (long long)(b % t.B2) * t.sb2;
+  T* dst = reinterpret_cast<T*>(t.dst) + plane * t.dst_plane + (long long)(b / t.B2) * t.db1 +
+           (long long)(b % t.B2) * t.db2;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    if (r < t.R && c < t.C) tile[k][threadIdx.x] = src[(long long)r * t.s_r + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    if (r < t.R && c < t.C) dst[(long long)c * t.d_c + (long long)r * t.d_r] = tile[threadIdx.x][k];
+  }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
@@ -277,23 +363,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int j = 0; j < 32; ++j) rr[j] = ri[j] = 0u;
         }
         if (m >= a.M) continue;
+        const int nb = n0 + c0;
         if (a.out_mode == TC_OUT_PARTIAL) {
           float2* P = a.partial + ((long long)blockIdx.z * a.M + m) * (long long)a.N;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const int n = n0 + c0 + j;
+            const int n = nb + j;
             if (n < a.N) P[n] = make_float2(__uint_as_float(rr[j]), __uint_as_float(ri[j]));
           }
         } else {
           for (int o = 0; o < a.nout; ++o) {
             const TcOutMap& om = a.out[o];
             const long long mo = (long long)(m / om.M2) * om.sM1 + (long long)(m % om.M2) * om.sM2;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int n = n0 + c0 + j;
-              if (n < a.N) {
-                const long long off = mo + (long long)(n / om.N2) * om.sN1 + (long long)(n % om.N2) * om.sN2;
-                put(om, a.fmt, off, __uint_as_float(rr[j]), __uint_as_float(ri[j]));
+            int n1 = nb / om.N2, n2 = nb % om.N2;
+            const long long off0 = mo + (long long)n1 * om.sN1 + n2;
+            const int vec = (a.fmt == TC_BF16) ? 8 : 4;  // elements per 16-byte store
+            if (om.sN2 == 1 && n2 + 32 <= om.N2 && nb + 32 <= a.N && (off0 % vec) == 0) {
+              put_row32(om, a.fmt, off0, rr, ri);
+            } else {
+              for (int j = 0; j < 32; ++j) {
+                if (nb + j < a.N)
+                  put(om, a.fmt, mo + (long long)n1 * om.sN1 + (long long)n2 * om.sN2, __uint_as_float(rr[j]),
+                      __uint_as_float(ri[j]));
+                if (++n2 == om.N2) {
+                  n2 = 0;
+                  ++n1;
+                }
               }
             }
           }
@@ -482,6 +577,19 @@ int tc_reduce_partials(const Launch& L, const float2* P, int splits, int M, int 
   const long long total = (long long)M * N;
   reduce_partials_kernel<<<grid_for(total, L.num_sms), 256, 0, L.stream>>>(P, splits, M, N,
                                                                            reinterpret_cast<double2*>(out), sm, sn);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int tc_transpose(const Launch& L, int fmt, const TcTranspose& t) {
+  if (t.R <= 0 || t.C <= 0 || t.batch <= 0) return 0;
+  const long long z = (long long)t.batch * tc_planes(fmt);
+  if (z > 65535 || (t.R + 31) / 32 > 65535) return TEVO_ESHAPE;
+  dim3 grid((t.C + 31) / 32, (t.R + 31) / 32, (unsigned)z), block(32, 8);
+  if (fmt == TC_BF16)
+    transpose_planes_kernel<unsigned short><<<grid, block, 0, L.stream>>>(t);
+  else
+    transpose_planes_kernel<unsigned int><<<grid, block, 0, L.stream>>>(t);
   ++*L.launches;
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
 }

@@ -49,6 +49,7 @@ struct DevMem {
 
 int grow(tevo_ctx c, DevMem& m, size_t bytes) {
   if (m.p && m.bytes >= bytes) return 0;
+  ++g_persist_gen;
   if (m.p) ctx_free(c, m.p);
   m.p = nullptr;
   m.bytes = 0;
@@ -68,7 +69,7 @@ struct MixedState {
   int fmt = -1;
   std::vector<size_t> env_off;
   std::vector<int> env_w;
-  DevMem env, Xt, T1, T2, site, Qp, part, err;
+  DevMem env, Xn, Xt, T1, T2, site, Qp, part, err;
 };
 
 namespace {
@@ -251,29 +252,54 @@ TcOperand w_operand(const DevMem& w, const Dims& k, int fmt) {
   return o;
 }
 
-// G1 + G2: T1 (optional) and T2 from (env view 1 of slot eb_left, site planes, W planes)
+// G1 + G2: T1 and T2 from (env view 1 of slot_left, site planes, W planes).
+// G1 writes X row-contiguous ([(p w)][(s' b)]); a batched transpose gives the
+// K-major X^T[(p b)][(w s')] that G2 reads; G2 writes T1 row-contiguous and a
+// second transpose gives T2 = T1^T for G3'.
 int make_T(tevo_ctx c, MixedState* m, const std::vector<int>& dims, int slot_left, const DevMem& Wp, const Dims& k,
            int fmt, bool want_T1) {
+  (void)want_T1;
   const Launch L = ctx_launch(c);
   const int P = P_(fmt);
-  // G1: X(m = (p w), n = (s' b)) -> X^T[(p b)][(w s')]
+  const long long npad = pad8((long long)k.d * k.Db);
+  const long long kp2 = pad8((long long)k.wl * k.d);
+  const long long bp = pad8(k.Db), kp4 = pad8((long long)k.Dp * k.d);
+  // G1: X(m = (p w), n = (s' b)) -> X[(p w)][(s' b)]
   {
-    const long long kp2 = pad8((long long)k.wl * k.d);
     TcArgs a = base_args(m);
     a.nout = 1;
-    a.out[0].base = m->Xt.p;
-    a.out[0].plane_stride = (long long)k.Dp * k.Db * kp2;
-    a.out[0].M2 = k.wl;
-    a.out[0].sM1 = (long long)k.Db * kp2;
-    a.out[0].sM2 = k.d;
-    a.out[0].N2 = k.Db;
-    a.out[0].sN1 = 1;
-    a.out[0].sN2 = kp2;
+    a.out[0].base = m->Xn.p;
+    a.out[0].plane_stride = (long long)k.Dp * k.wl * npad;
+    a.out[0].M2 = 1 << 30;
+    a.out[0].sM1 = 0;
+    a.out[0].sM2 = npad;
+    a.out[0].N2 = 1 << 30;
+    a.out[0].sN1 = 0;
+    a.out[0].sN2 = 1;
     TRY(tc_gemm(L, fmt, env_view1(m, dims, slot_left, fmt), site_operand(m, k, fmt), k.Dp * k.wl, k.d * k.Db, a));
   }
-  // G2: T(m = (s v), n = (p b)) -> T1[(p s)][v][b], T2[(v b)][(p s)]
+  // X^T[(p b)][(w s')]: per (p, s'), transpose the wl x Db block
   {
-    const long long kp2 = pad8((long long)k.wl * k.d);
+    TcTranspose t;
+    t.src = m->Xn.p;
+    t.dst = m->Xt.p;
+    t.src_plane = (long long)k.Dp * k.wl * npad;
+    t.dst_plane = (long long)k.Dp * k.Db * kp2;
+    t.batch = k.Dp * k.d;
+    t.B2 = k.d;
+    t.sb1 = (long long)k.wl * npad;
+    t.sb2 = k.Db;
+    t.db1 = (long long)k.Db * kp2;
+    t.db2 = 1;
+    t.R = k.wl;
+    t.C = k.Db;
+    t.s_r = npad;
+    t.d_c = kp2;
+    t.d_r = k.d;
+    TRY(tc_transpose(L, fmt, t));
+  }
+  // G2: T(m = (s v), n = (p b)) -> T1[(p s)][v][b]
+  {
     TcOperand B;
     B.base = m->Xt.p;
     B.elem_bytes = EB(fmt);
@@ -285,32 +311,37 @@ int make_T(tevo_ctx c, MixedState* m, const std::vector<int>& dims, int slot_lef
     B.k_out = 1;
     B.kout_pitch = kp2;
     TcArgs a = base_args(m);
-    int no = 0;
-    const long long bp = pad8(k.Db), kp4 = pad8((long long)k.Dp * k.d);
-    if (want_T1) {
-      TcOutMap& o = a.out[no++];
-      o.base = m->T1.p;
-      o.plane_stride = (long long)k.Dp * k.d * k.wr * bp;
-      o.M2 = k.wr;
-      o.sM1 = (long long)k.wr * bp;
-      o.sM2 = bp;
-      o.N2 = k.Db;
-      o.sN1 = (long long)k.d * k.wr * bp;
-      o.sN2 = 1;
-    }
-    {
-      TcOutMap& o = a.out[no++];
-      o.base = m->T2.p;
-      o.plane_stride = (long long)k.wr * k.Db * kp4;
-      o.M2 = k.wr;
-      o.sM1 = 1;
-      o.sM2 = (long long)k.Db * kp4;
-      o.N2 = k.Db;
-      o.sN1 = k.d;
-      o.sN2 = kp4;
-    }
-    a.nout = no;
+    TcOutMap& o = a.out[0];
+    o.base = m->T1.p;
+    o.plane_stride = (long long)k.Dp * k.d * k.wr * bp;
+    o.M2 = k.wr;
+    o.sM1 = (long long)k.wr * bp;
+    o.sM2 = bp;
+    o.N2 = k.Db;
+    o.sN1 = (long long)k.d * k.wr * bp;
+    o.sN2 = 1;
+    a.nout = 1;
     TRY(tc_gemm(L, fmt, w_operand(Wp, k, fmt), B, k.d * k.wr, k.Dp * k.Db, a));
+  }
+  // T2[(v b)][(p s)] = T1^T, batched over v
+  {
+    TcTranspose t;
+    t.src = m->T1.p;
+    t.dst = m->T2.p;
+    t.src_plane = (long long)k.Dp * k.d * k.wr * bp;
+    t.dst_plane = (long long)k.wr * k.Db * kp4;
+    t.batch = k.wr;
+    t.B2 = k.wr;
+    t.sb1 = 0;
+    t.sb2 = bp;
+    t.db1 = 0;
+    t.db2 = (long long)k.Db * kp4;
+    t.R = k.Dp * k.d;
+    t.C = k.Db;
+    t.s_r = (long long)k.wr * bp;
+    t.d_c = kp4;
+    t.d_r = 1;
+    TRY(tc_transpose(L, fmt, t));
   }
   return 0;
 }
@@ -401,6 +432,7 @@ int mixed_prepare(tevo_ctx c, tevo_mpo W, tevo_mps s, int precision) {
   MixedMPO*& mm = mpo_mixed(W);
   if (!mm) mm = new MixedMPO;
   if (mm->fmt != fmt) {
+    ++g_persist_gen;
     mm->Wr.resize(L);
     mm->Wl.resize(L);
     for (int i = 0; i < L; ++i) {
@@ -441,11 +473,12 @@ int mixed_prepare(tevo_ctx c, tevo_mpo W, tevo_mps s, int precision) {
     off += al((size_t)P * env_plane_stride(dims, m->env_w[b], b) * eb);
   }
   TRY(grow(c, m->env, off));
-  size_t xt = 0, t1 = 0, t2 = 0, site = 0, qp = 0, part = 0;
+  size_t xn = 0, xt = 0, t1 = 0, t2 = 0, site = 0, qp = 0, part = 0;
   for (int i = 0; i < L; ++i) {
     for (int side = 0; side < 2; ++side) {
       Dims k = side == 0 ? right_dims(W, dims, d, i) : left_dims(W, dims, d, i);
       xt = std::max<size_t>(xt, (size_t)P * k.Dp * k.Db * pad8((long long)k.wl * k.d) * eb);
+      xn = std::max<size_t>(xn, (size_t)P * k.Dp * k.wl * pad8((long long)k.d * k.Db) * eb);
       t1 = std::max<size_t>(t1, (size_t)P * k.Dp * k.d * k.wr * pad8(k.Db) * eb);
       t2 = std::max<size_t>(t2, (size_t)P * k.wr * k.Db * pad8((long long)k.Dp * k.d) * eb);
       site = std::max<size_t>(site, (size_t)P * k.d * k.Db * pad8(k.Da) * eb);
@@ -453,6 +486,7 @@ int mixed_prepare(tevo_ctx c, tevo_mpo W, tevo_mps s, int precision) {
       part = std::max<size_t>(part, (size_t)64 * k.Dp * k.d * k.Dq * 8);
     }
   }
+  TRY(grow(c, m->Xn, al(xn)));
   TRY(grow(c, m->Xt, al(xt)));
   TRY(grow(c, m->T1, al(t1)));
   TRY(grow(c, m->T2, al(t2)));
@@ -606,7 +640,7 @@ void mixed_mpo_destroy(tevo_ctx c, MixedMPO*& m) {
 
 void mixed_state_destroy(tevo_ctx c, MixedState*& m) {
   if (!m) return;
-  for (DevMem* d : {&m->env, &m->Xt, &m->T1, &m->T2, &m->site, &m->Qp, &m->part, &m->err})
+  for (DevMem* d : {&m->env, &m->Xn, &m->Xt, &m->T1, &m->T2, &m->site, &m->Qp, &m->part, &m->err})
     if (d->p) ctx_free(c, d->p);
   delete m;
   m = nullptr;

@@ -17,6 +17,10 @@ typedef CUstream_st* cudaStream_t;
 
 namespace tevo {
 
+// bumped whenever a persistent device buffer of a handle is (re)allocated;
+// captured CUDA graphs of the batched form are dropped when it changes
+extern long long g_persist_gen;
+
 // host MPO construction (mpo_build.cpp)
 int build_mpo_host(int L, int d, int chi, const double* A, const double* B, const double* C,
                    const double* Dh, int N, double tau_re, double tau_im, int variant,

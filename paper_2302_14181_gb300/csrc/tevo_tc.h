@@ -71,6 +71,19 @@ struct TcConvert {
   int kin;          // K index k -> (k / kin) * kout_pitch + k % kin
 };
 
+// batched plane transpose: for every plane and batch index b (split b = (b / B2, b % B2)),
+// dst[c * d_c + r * d_r] = src[r * s_r + c] for r < R, c < C (offsets in elements,
+// relative to the batch bases (b / B2) * sb1 + (b % B2) * sb2 and db1, db2)
+struct TcTranspose {
+  const void* src;
+  void* dst;
+  long long src_plane, dst_plane;
+  int batch, B2;
+  long long sb1, sb2, db1, db2;
+  int R, C;
+  long long s_r, d_c, d_r;
+};
+
 int tc_planes(int fmt);
 int tc_elem_bytes(int fmt);
 int tc_kchunk(int fmt);
@@ -78,6 +91,7 @@ int tc_gemm(const Launch& L, int fmt, const TcOperand& A, const TcOperand& B, in
 int tc_to_planes(const Launch& L, const TcConvert& c);
 int tc_reduce_partials(const Launch& L, const float2* P, int splits, int M, int N, void* out, long long sm,
                        long long sn);
+int tc_transpose(const Launch& L, int fmt, const TcTranspose& t);
 int tc_zero_planes(const Launch& L, const TcOutMap& o, int fmt, long long n);
 
 }  // namespace tevo
