@@ -33,7 +33,8 @@ import workloads as wl  # noqa: E402
 
 METRIC = "W^(N)·MPS fit sweeps/s & TFLOP/s vs peak at ≤1e-6 obs error, mixed vs FP64"
 WORKLOAD = "lri_L100_N3_D256"
-PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3}
+PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3,
+        "tc-tf32": 0x101, "tc-tf32x3": 0x102, "tc-bf16x3": 0x103}
 # fp64 issue rate on GB300: 2 DFMA per clock per SM (152 SMs, 2070 MHz max SM clock)
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 
@@ -284,6 +285,29 @@ def our_arm(args):
     launches = ctx.launch_count()
     prof = {c: ctx.prof_read(c) for c in range(4)}
     value, ms_max = replica_throughput(ms, args.steps * sweeps, "cuda")
+    # observables after warmup + steps time steps against the oracle's stored values
+    obs_err = None
+    gpath = os.path.join(ROOT, "tests", "golden", WORKLOAD + ".json")
+    nstep = args.warmup + args.steps
+    if os.path.exists(gpath):
+        g = json.load(open(gpath))
+        if str(nstep) in g["steps"] and g["config"]["sweeps"] == sweeps:
+            ref = np.array(g["steps"][str(nstep)])
+            got = tv.measure_local(psi, list(wl.pauli())).real
+            obs_err = {"step": nstep, "t": nstep * abs(tau), "max_abs": float(np.abs(got - ref).max()),
+                       "against": "fp64 oracle (tests/golden)"}
+    # the plain fp64 form, one step from the same state, for the mixed-vs-fp64 comparison
+    fp64_form = None
+    if prec != 0 and not args.no_fp64_compare:
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        tv.evolve_step(psi, W, tau, D, sweeps, tv.FP64)
+        f1.record(stream)
+        barrier()
+        fms = f0.elapsed_time(f1)
+        fp64_form = {"value": sweeps / (fms / 1e3), "unit": "sweeps/s", "ms_per_step": fms, "sweeps": sweeps,
+                     "speedup_of_measured_form": (fms / (ms_max / args.steps))}
 
     # end to end through the public API with host buffers (pinned), every step:
     # upload the state, evolve, read observables and the state back
@@ -310,24 +334,37 @@ def our_arm(args):
 
     if rank == 0:
         peaks, src = load_peaks()
-        cls = tv._lib.PROF_GEMM64 if prec == 0 else tv._lib.PROF_GEMMTC
-        kms, kn, kfl, kby = prof[cls]
-        if prec == 0:
+        def fp64_roof(kms, kn, kfl):
             achieved = kfl / (kms / 1e3) / 1e12 if kms > 0 else None
-            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
                     "traffic": traffic_from_profiles("zgemm_kernel"),
                     "kernel": "zgemm_kernel (fp64 complex GEMM)", "launches": kn,
                     "avg_launch_ms": kms / kn if kn else None,
                     "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (fp64 pipe)"}
-        else:
-            peak = peaks.get("bf16_tflops_sustained", 1700.0) * (0.5 if prec in (1, 2) else 1.0)
-            achieved = kfl / (kms / 1e3) / 1e12 if kms > 0 else None
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak if achieved else None, "traffic": traffic_from_profiles("tc_gemm"),
-                    "kernel": "tcgen05 complex GEMM", "launches": kn,
-                    "avg_launch_ms": kms / kn if kn else None,
-                    "peak_source": f"{src} bf16 sustained" + (" x 0.5 (tf32)" if prec in (1, 2) else "")}
+
+        def tc_roof(kms, kn, kfl):
+            base = prec & 0xFF
+            passes = 1 if base == 1 else 3
+            peak = peaks.get("bf16_tflops_sustained", 1700.0) * (0.5 if base in (1, 2) else 1.0)
+            achieved = passes * kfl / (kms / 1e3) / 1e12 if kms > 0 else None
+            return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak if achieved else None, "traffic": traffic_from_profiles("tc_gemm_kernel"),
+                    "kernel": "tc_gemm_kernel (tcgen05 complex GEMM; executed flops = useful x passes)",
+                    "launches": kn, "avg_launch_ms": kms / kn if kn else None, "passes": passes,
+                    "useful_tflops": kfl / (kms / 1e3) / 1e12 if kms > 0 else None,
+                    "peak_source": f"{src} bf16 sustained" + (" x 0.5 (tf32)" if base in (1, 2) else "")}
+
+        g64, gtc = prof[tv._lib.PROF_GEMM64], prof[tv._lib.PROF_GEMMTC]
+        roofs = {}
+        if g64[0] > 0:
+            roofs["fp64_gemm"] = fp64_roof(g64[0], g64[1], g64[2])
+        if gtc[0] > 0:
+            roofs["tc_gemm"] = tc_roof(gtc[0], gtc[1], gtc[2])
+        dominant = "fp64_gemm" if g64[0] >= gtc[0] else "tc_gemm"
+        roof = dict(roofs[dominant])
+        roof["dominant_by_time"] = True
+        other = [k for k in roofs if k != dominant]
         cpu = oracle_sample(cfg, seconds=args.cpu_seconds)
         line = {
             "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
@@ -341,6 +378,7 @@ def our_arm(args):
                        "parallelism": f"replicas x{world}"},
             "tflops": flops * args.steps * world / (ms_max / 1e3) / 1e12,
             "roofline": roof,
+            "roofline_other": {k: roofs[k] for k in other},
             "cpu_baseline": {"value": cpu["sweeps_per_s"], "unit": "sweeps/s", "cores": cpu["cores"],
                              "kind": "oracle",
                              "sample": f"{cpu['updates']} oracle local updates at the interior-site shape "
@@ -348,6 +386,8 @@ def our_arm(args):
                                        f"evolve_step of the L=100 chain"},
             "e2e": {"value": e2e_val, "unit": "sweeps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
+            "obs_error": obs_err,
+            "fp64_form": fp64_form,
             "clocks": clocks.summary(),
             "kernel_ms": {name: prof[c][0] for c, name in enumerate(["gemm64", "gemm_tc", "qr", "form_q"])},
         }
@@ -362,7 +402,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("TEVO_BENCH_PRECISION", "fp64"), choices=sorted(PREC))
+    ap.add_argument("--precision", default=os.environ.get("TEVO_BENCH_PRECISION", "bf16x3"), choices=sorted(PREC))
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip the fp64-form step timed beside the mixed form")
     ap.add_argument("--sweeps", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
