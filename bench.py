@@ -396,6 +396,40 @@ def our_arm(args):
         dist.destroy_process_group()
 
 
+def verify(args):
+    """The target check: the full evolution to t = 5 (25 steps) in each form,
+    observables against the oracle's stored values at every recorded step."""
+    import torch
+    import paper_2302_14181_gb300 as tv
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cfg = wl.config(WORKLOAD)
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", WORKLOAD + ".json")))
+    ctx = tv.Context()
+    W = tv.mpo_build(ctx, *wl.model_blocks(cfg), cfg["N"], cfg["tau"])
+    ops = list(wl.pauli())
+    out = {"workload": WORKLOAD, "steps": cfg["steps"], "t": cfg["steps"] * abs(cfg["tau"]), "forms": {}}
+    forms = args.verify_forms.split(",")
+    for form in forms:
+        prec = PREC[form]
+        psi = tv.mps_init(ctx, wl.initial_vectors(cfg), cfg["D"])
+        errs, t_total = {}, 0.0
+        for k in range(1, cfg["steps"] + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tv.evolve_step(psi, W, cfg["tau"], cfg["D"], cfg["sweeps"], prec)
+            torch.cuda.synchronize()
+            t_total += time.perf_counter() - t0
+            if str(k) in g["steps"]:
+                ref = np.array(g["steps"][str(k)])
+                got = tv.measure_local(psi, ops).real
+                errs[k] = float(np.abs(got - ref).max())
+        out["forms"][form] = {"max_abs_obs_error_by_step": errs, "max_abs_obs_error": max(errs.values()),
+                              "log_norm": psi.log_norm(), "log_norm_oracle": g["log_norm"][-1],
+                              "seconds": t_total, "s_per_step": t_total / cfg["steps"]}
+        print(json.dumps({"form": form, **out["forms"][form]}), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -406,7 +440,12 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the fp64-form step timed beside the mixed form")
     ap.add_argument("--sweeps", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--verify", action="store_true", help="run the t = 5 evolution in each form against the oracle")
+    ap.add_argument("--verify-forms", default="tc-tf32x3,tc-bf16x3,bf16x3,fp64")
     args = ap.parse_args()
+    if args.verify:
+        verify(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:
