@@ -228,6 +228,15 @@ int tevo_gemm(tevo_ctx ctx, int precision, int M, int N, int K, const double* A,
 int tevo_gemm_noalloc(tevo_ctx ctx, int precision, int M, int N, int K, const double* A, const double* B,
                       double* C);
 
+/*
+ * tevo_wait_selftest -- exercises the bounded device-side wait used by the
+ * tensor-core kernels: one thread waits on a shared-memory barrier that nothing
+ * completes, gives up after limit_ms (0 < limit_ms <= 5000) and records a code
+ * in a device flag, which is copied to *code. Returns TEVO_ETIMEOUT when the
+ * wait gave up (the expected outcome); the context stays usable.
+ */
+int tevo_wait_selftest(tevo_ctx ctx, double limit_ms, int* code);
+
 /* name of an error code */
 const char* tevo_strerror(int code);
 

@@ -63,6 +63,7 @@ _SIGS = {
     "mps_overlap": [tevo_mps, tevo_mps, _pd, _pd],
     "tevo_gemm": [tevo_ctx, _i, _i, _i, _i, _p, _p, _p],
     "tevo_gemm_noalloc": [tevo_ctx, _i, _i, _i, _i, _p, _p, _p],
+    "tevo_wait_selftest": [tevo_ctx, _d, _pi],
     "tevo_prof_enable": [tevo_ctx, _i],
     "tevo_prof_read": [tevo_ctx, _i, _pd, ctypes.POINTER(ctypes.c_longlong), _pd, _pd],
 }

@@ -28,6 +28,7 @@
 
 #include "tevo_internal.h"
 #include "tevo_mixed.h"
+#include "tevo_tc.h"
 
 using namespace tevo;
 
@@ -1108,6 +1109,20 @@ extern "C" int tevo_gemm_noalloc(tevo_ctx c, int precision, int M, int N, int K,
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15)
     return TEVO_EINVAL;
   return noalloc_gemm(launch_of(c), precision, M, N, K, A, B, C);
+}
+
+extern "C" int tevo_wait_selftest(tevo_ctx c, double limit_ms, int* code) {
+  if (!c || !code || !(limit_ms > 0) || limit_ms > 5000) return TEVO_EINVAL;
+  Buf flag;
+  TRY(dalloc(c, flag, 256));
+  int e = cudaMemsetAsync(flag.p, 0, sizeof(int), c->stream) == cudaSuccess ? 0 : TEVO_ECUDA;
+  if (!e) e = tc_wait_selftest(launch_of(c), static_cast<int*>(flag.p), limit_ms);
+  if (!e && (cudaMemcpyAsync(code, flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+             cudaStreamSynchronize(c->stream) != cudaSuccess))
+    e = TEVO_ECUDA;
+  dfree(c, flag);
+  if (e) return e;
+  return *code ? TEVO_ETIMEOUT : 0;
 }
 
 extern "C" int mps_overlap(tevo_mps a, tevo_mps b, double* log_abs, double* phase) {

@@ -19,13 +19,17 @@
 // is itself two tensor modes with a padded inner mode (an environment's
 // (w, psi) legs) is read through TMA bounds checks instead of padding.
 //
-// CTA tile 128 (M) x 256 (N); Cr occupies tensor-memory columns [0, 256) and
-// Ci [256, 512). K chunk = 64 bytes per row (32 bf16 / 16 fp32), 64B swizzle,
-// two pipeline stages of 96 KB.
+// Persistent kernel: one CTA per SM walks the tiles (128 x 128 complex outputs,
+// split-K chunks included) in a static round-robin order. Tensor memory holds
+// two accumulator buffers (Cr, Ci of 128 columns each), so the epilogue warps
+// drain tile i while the MMA warp accumulates tile i+1; the TMA producer runs
+// ahead across tiles through a 3-stage ring of 64 KB stages (K chunk = 64 bytes
+// per row: 32 bf16 / 16 fp32, 64B swizzle).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -36,11 +40,11 @@ namespace tevo {
 
 namespace {
 
-constexpr int TM = 128, TN = 256;
+constexpr int TM = 128, TN = 128;
 constexpr int KCB = 64;  // bytes of K per stage row
-constexpr int NSTAGE = 2;
+constexpr int NSTAGE = 3;
 constexpr int A_BYTES = 4 * TM * KCB;  // 32 KB (4 planes max)
-constexpr int B_BYTES = 4 * TN * KCB;  // 64 KB
+constexpr int B_BYTES = 4 * TN * KCB;  // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int TC_THREADS = 192;
@@ -68,12 +72,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 
 // wait on an mbarrier phase with a time limit; false (and the error flag set)
 // when the limit passes
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code,
+                          unsigned long long limit_ns = WAIT_NS) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   while (true) {
     if (mbar_try(bar, parity)) return true;
-    if (gtimer() - t0 > WAIT_NS) {
+    if (gtimer() - t0 > limit_ns) {
       atomicExch(err, code);
       return false;
     }
@@ -87,6 +92,19 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+
+// self-test of the bounded wait: one thread waits on a barrier that nothing
+// completes; the wait gives up after limit_ns and records `code`
+__global__ void wait_selftest_kernel(int* err, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, err, 7, limit_ns);
+}
+
 
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
                                             uint32_t bar) {
@@ -259,21 +277,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSTAGE + 1);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSTAGE), accb = smem_u32(bars + 2 * NSTAGE);
+  // barriers: full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2]; then the TMEM address slot
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSTAGE + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSTAGE);
+  const uint32_t tfull0 = smem_u32(bars + 2 * NSTAGE), tempty0 = smem_u32(bars + 2 * NSTAGE + 2);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
-  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
-  const int kt0 = blockIdx.z * a.tiles_per_split;
-  const int kt1 = min(a.k_tiles, kt0 + a.tiles_per_split);
-  const int nk = kt1 > kt0 ? kt1 - kt0 : 0;
+  const int mt = (a.M + TM - 1) / TM, nt = (a.N + TN - 1) / TN;
+  const int ntiles = mt * nt * a.splits;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(accb, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 4);  // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -285,76 +306,107 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const int planes = a.planes;
-  const uint32_t bytesA = planes * TM * KCB, bytesB = planes * TN * KCB;
+  const uint32_t bytesA = a.planes * TM * KCB, bytesB = a.planes * TN * KCB;
+
+  // tile t -> (split z, row tile y, column tile x) and its K-tile range
+  auto tile_of = [&](int t, int& m0, int& n0, int& kt0, int& kt1) {
+    const int z = t / (mt * nt), r = t % (mt * nt);
+    m0 = (r / nt) * TM;
+    n0 = (r % nt) * TN;
+    kt0 = z * a.tiles_per_split;
+    kt1 = min(a.k_tiles, kt0 + a.tiles_per_split);
+    if (kt1 < kt0) kt1 = kt0;
+    return z;
+  };
 
   if (warp == 0) {
-    if (lane == 0 && nk > 0) {
+    if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
       const int kc_elems = KCB / a.elem_bytes;
-      int issued = 0;
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % NSTAGE;
-        const uint32_t ph = (i / NSTAGE) & 1;
-        if (!mbar_wait(empty0 + 8 * s, ph ^ 1, a.err, 1)) break;
-        const uint32_t fb = full0 + 8 * s;
-        mbar_expect_tx(fb, bytesA + bytesB);
-        const int kt = kt0 + i;
-        const int ko = kt / a.k_in_chunks, kc = (kt % a.k_in_chunks) * kc_elems;
-        uint8_t* st = smem + s * STAGE_BYTES;
-        tma_load_4d(smem_u32(st), &tmA, kc, ko, m0, 0, fb);
-        tma_load_4d(smem_u32(st + A_BYTES), &tmB, kc, ko, n0, 0, fb);
-        issued = i + 1;
+      long long g = 0;  // stage ring counter across tiles
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int m0, n0, kt0, kt1;
+        tile_of(t, m0, n0, kt0, kt1);
+        for (int kt = kt0; kt < kt1; ++kt, ++g) {
+          const int s = int(g % NSTAGE);
+          const uint32_t ph = uint32_t(g / NSTAGE) & 1u;
+          if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, a.err, 1)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = full0 + 8 * s;
+          mbar_expect_tx(fb, bytesA + bytesB);
+          const int ko = kt / a.k_in_chunks, kc = (kt % a.k_in_chunks) * kc_elems;
+          uint8_t* st = smem + s * STAGE_BYTES;
+          tma_load_4d(smem_u32(st), &tmA, kc, ko, m0, 0, fb);
+          tma_load_4d(smem_u32(st + A_BYTES), &tmB, kc, ko, n0, 0, fb);
+        }
       }
-      // do not leave while copies are in flight: wait for the stages just filled
-      for (int i = (issued > NSTAGE ? issued - NSTAGE : 0); i < issued; ++i)
-        mbar_wait(full0 + 8 * (i % NSTAGE), (i / NSTAGE) & 1, a.err, 2);
+      // do not leave while copies are in flight: wait for the last stages filled
+      for (long long q = (g > NSTAGE ? g - NSTAGE : 0); q < g; ++q)
+        mbar_wait(full0 + 8 * int(q % NSTAGE), uint32_t(q / NSTAGE) & 1u, a.err, 2);
     }
   } else if (warp == 1) {
-    if (lane == 0 && nk > 0) {
-      // instruction descriptor: fp32 accumulate, K-major A and B, M = 128, N = 256
+    if (lane == 0) {
+      // instruction descriptor: fp32 accumulate, K-major A and B, M = TM, N = TN
       const uint32_t fmtAB = (KIND == TC_BF16) ? 1u : 2u;
       const uint32_t base_id = (1u << 4) | (fmtAB << 7) | (fmtAB << 10) | ((uint32_t)(TN >> 3) << 17) |
                                ((uint32_t)(TM >> 4) << 24);
-      bool started[2] = {false, false};
+      long long g = 0;
+      int i = 0;  // local tile count
       bool ok = true;
-      for (int i = 0; i < nk && ok; ++i) {
-        const int s = i % NSTAGE;
-        const uint32_t ph = (i / NSTAGE) & 1;
-        if (!mbar_wait(full0 + 8 * s, ph, a.err, 3)) {
-          ok = false;
-          break;
-        }
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        int m0, n0, kt0, kt1;
+        tile_of(t, m0, n0, kt0, kt1);
+        const int b = i & 1;
+        // the epilogue must have drained this accumulator buffer (first use passes)
+        if (!mbar_wait(tempty0 + 8 * b, (uint32_t(i >> 1) & 1u) ^ 1u, a.err, 5)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
-#pragma unroll
-        for (int ks = 0; ks < KCB / 32; ++ks) {
-          for (int p = 0; p < a.nprod; ++p) {
-            const uint64_t ad = sdesc(sa + a.a_plane[p] * TM * KCB + ks * 32);
-            const uint64_t bd = sdesc(sb + a.b_plane[p] * TN * KCB + ks * 32);
-            const int acc = a.acc[p];
-            const uint32_t id = base_id | (a.neg[p] ? (1u << 13) : 0u);
-            mma<KIND>(tmem + acc * TN, ad, bd, id, started[acc] ? 1u : 0u);
-            started[acc] = true;
+        const uint32_t dbase = tmem + (uint32_t)(b * 2 * TN);
+        bool started[2] = {false, false};
+        for (int kt = kt0; kt < kt1; ++kt, ++g) {
+          const int s = int(g % NSTAGE);
+          const uint32_t ph = uint32_t(g / NSTAGE) & 1u;
+          if (!mbar_wait(full0 + 8 * s, ph, a.err, 3)) {
+            ok = false;
+            break;
           }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
+#pragma unroll
+          for (int ks = 0; ks < KCB / 32; ++ks) {
+            for (int p = 0; p < a.nprod; ++p) {
+              const uint64_t ad = sdesc(sa + a.a_plane[p] * TM * KCB + ks * 32);
+              const uint64_t bd = sdesc(sb + a.b_plane[p] * TN * KCB + ks * 32);
+              const int acc = a.acc[p];
+              const uint32_t id = base_id | (a.neg[p] ? (1u << 13) : 0u);
+              mma<KIND>(dbase + acc * TN, ad, bd, id, started[acc] ? 1u : 0u);
+              started[acc] = true;
+            }
+          }
+          mma_commit(empty0 + 8 * s);
         }
-        mma_commit(empty0 + 8 * s);
+        mma_commit(tfull0 + 8 * b);
       }
-      mma_commit(accb);
     }
   } else {
     // epilogue: warps 2..5 own tensor-memory lane quarters (warp % 4)
     const int q = warp % 4;
-    const int m = m0 + q * 32 + lane;
-    bool ok = true;
-    if (nk > 0) ok = mbar_wait(accb, 0, a.err, 4);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      int m0, n0, kt0, kt1;
+      const int z = tile_of(t, m0, n0, kt0, kt1);
+      const bool has_k = kt1 > kt0;
+      const int b = i & 1;
+      if (!mbar_wait(tfull0 + 8 * b, uint32_t(i >> 1) & 1u, a.err, 4)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int m = m0 + q * 32 + lane;
+      const uint32_t trow = tmem + (uint32_t)(b * 2 * TN) + ((uint32_t)(q * 32) << 16);
       for (int c0 = 0; c0 < TN; c0 += 32) {
         uint32_t rr[32], ri[32];
-        if (nk > 0) {
+        if (has_k) {
           tmem_ld32(trow + c0, rr);
           tmem_ld32(trow + TN + c0, ri);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -365,7 +417,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (m >= a.M) continue;
         const int nb = n0 + c0;
         if (a.out_mode == TC_OUT_PARTIAL) {
-          float2* P = a.partial + ((long long)blockIdx.z * a.M + m) * (long long)a.N;
+          float2* P = a.partial + ((long long)z * a.M + m) * (long long)a.N;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int n = nb + j;
@@ -394,11 +446,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
+      // this warp is done reading the buffer: hand it back to the MMA warp
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8 * b) : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
+    __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
@@ -549,8 +606,10 @@ int tc_gemm(const Launch& L, int fmt, const TcOperand& A, const TcOperand& B, in
   splits = (args.k_tiles + args.tiles_per_split - 1) / args.tiles_per_split;
   args.splits = splits;
   tc_products(fmt, args);
-  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, splits);
-  if (grid.y > 65535 || grid.z > 65535) return TEVO_ESHAPE;
+  const long long ntiles = (long long)((N + TN - 1) / TN) * ((M + TM - 1) / TM) * splits;
+  if (ntiles > (1LL << 30)) return TEVO_ESHAPE;
+  // persistent: one CTA per SM (shared memory allows no more), static tile loop
+  dim3 grid((unsigned)std::min<long long>(ntiles, (long long)L.num_sms));
   const double useful = 8.0 * (double)M * N * (double)A.k_in * A.k_out;
   int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_GEMMTC, useful,
                                   (double)A.elem_bytes * A.planes * ((double)M + N) * A.k_in * A.k_out)
@@ -590,6 +649,12 @@ int tc_transpose(const Launch& L, int fmt, const TcTranspose& t) {
     transpose_planes_kernel<unsigned short><<<grid, block, 0, L.stream>>>(t);
   else
     transpose_planes_kernel<unsigned int><<<grid, block, 0, L.stream>>>(t);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int tc_wait_selftest(const Launch& L, int* err_dev, double limit_ms) {
+  wait_selftest_kernel<<<1, 32, 0, L.stream>>>(err_dev, (unsigned long long)(limit_ms * 1e6));
   ++*L.launches;
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
 }

@@ -362,7 +362,7 @@ int apply_tc(tevo_ctx c, MixedState* m, const std::vector<int>& dims, int slot_r
   A.k_out = k.wr;
   A.kout_pitch = bp;
   const int M = k.Dp * k.d, N = k.Dq;
-  const int tiles = ((M + 127) / 128) * ((N + 255) / 256);
+  const int tiles = ((M + 127) / 128) * ((N + 127) / 128);
   const int kc = tc_kchunk(fmt);
   const int ktiles = ((k.Db + kc - 1) / kc) * k.wr;
   int splits = std::max(1, std::min(num_sms / std::max(1, tiles), ktiles / 2));
@@ -573,7 +573,7 @@ int mixed_gemm(tevo_ctx c, int precision, int M, int N, int K, const void* A, co
   const int P = P_(fmt), eb = EB(fmt);
   const Launch L = ctx_launch(c);
   const long long kp = pad8(K);
-  const int tiles = ((M + 127) / 128) * ((N + 255) / 256);
+  const int tiles = ((M + 127) / 128) * ((N + 127) / 128);
   const int kc = tc_kchunk(fmt);
   const int ktiles = (K + kc - 1) / kc;
   int splits = std::max(1, std::min({L.num_sms / std::max(1, tiles), ktiles, 64}));

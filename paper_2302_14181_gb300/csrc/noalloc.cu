@@ -78,7 +78,7 @@ size_t noalloc_need(int precision, int M, int N, int K, int num_sms, int* splits
   const long long kp = pad8(K);
   const size_t planes = al256((size_t)P * M * kp * eb) + al256((size_t)P * N * kp * eb);
   if (256 + planes + al256((size_t)M * N * 8) > limit) return 0;
-  const int tiles = ((M + 127) / 128) * ((N + 255) / 256);
+  const int tiles = ((M + 127) / 128) * ((N + 127) / 128);
   const int kc = tc_kchunk(fmt);
   const int ktiles = (K + kc - 1) / kc;
   int splits = std::max(1, std::min({num_sms / std::max(1, tiles), ktiles, 64}));

@@ -92,6 +92,7 @@ int tc_to_planes(const Launch& L, const TcConvert& c);
 int tc_reduce_partials(const Launch& L, const float2* P, int splits, int M, int N, void* out, long long sm,
                        long long sn);
 int tc_transpose(const Launch& L, int fmt, const TcTranspose& t);
+int tc_wait_selftest(const Launch& L, int* err_dev, double limit_ms);
 int tc_zero_planes(const Launch& L, const TcOutMap& o, int fmt, long long n);
 
 }  // namespace tevo

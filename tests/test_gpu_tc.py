@@ -103,3 +103,13 @@ def test_mixed_lri_ragged(ctx):
         psi_o, _ = fit.evolve_step(psi_o, Wo, 2, canonical=k > 0)
         tv.evolve_step(psi, W, tau, D, 2, tv.BF16X3)
     assert rel_err(tv.measure_local(psi, ops).real, fit.measure_local(psi_o, ops).real) < 1e-6
+
+
+def test_bounded_wait_gives_up_and_context_survives(ctx):
+    """A device wait on a barrier that nothing completes ends after its limit with
+    an error status (TEVO_ETIMEOUT) instead of hanging; the context still works."""
+    code = ctypes.c_int(0)
+    rc = tv._lib.lib.tevo_wait_selftest(ctx.handle, 50.0, ctypes.byref(code))
+    assert rc == -7 and code.value == 7
+    A = np.ones((4, 3), np.complex128)
+    assert np.allclose(tc_gemm(ctx, tv.BF16X3, A, A), A @ A.T)
