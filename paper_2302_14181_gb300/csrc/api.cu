@@ -105,6 +105,8 @@ struct tevo_mpo_s {
   double tau_re = 0, tau_im = 0;
   std::vector<int> wl, wr;
   std::vector<Buf> W, Wr, Wl;
+  // nonzeros of Wr / Wl as CSR (row_ptr | col_idx ints, values complex) for G2
+  std::vector<Buf> Sr_idx, Sr_val, Sl_idx, Sl_val;
   std::vector<std::vector<std::complex<double>>> host;  // W_i on the host (test access)
   MixedMPO* mixed = nullptr;                            // low-precision operands (lazy)
 };
@@ -169,11 +171,20 @@ struct StepDims {
   int Dp, Da, wl, d, Db, Dq, wr;
 };
 
-// G1 + G2: T from (El, A, Wg) in fp64
-int make_T64(tevo_mps s, const StepDims& k, const z64* El, const z64* A, const z64* Wg) {
+// G1 + G2: T from (El, A, Wg) in fp64; G2 skips the MPO's zero entries when
+// its CSR form (sidx = row_ptr then col_idx, sval) is given
+int make_T64(tevo_mps s, const StepDims& k, const z64* El, const z64* A, const z64* Wg, const Buf* sidx = nullptr,
+             const Buf* sval = nullptr) {
   // G1: X[(p w), (s' b)] = El[(p w), a] A[a, (s' b)]
   TRY(gemm(s, gd(El, 0, k.Da, 1, A, 0, (long long)k.d * k.Db, 1, s->X.p, 0, (long long)k.d * k.Db, 1,
                  k.Dp * k.wl, k.d * k.Db, k.Da, 1)));
+  if (sidx && sidx->p) {
+    const int R = k.d * k.wr;
+    const int* rp = static_cast<const int*>(sidx->p);
+    int e = zsparse_g2(launch_of(s->ctx), zp(s->X), zp(s->T), rp, rp + R + 1, static_cast<const z64*>(sval->p), R,
+                       k.wl * k.d, k.Db, k.Dp);
+    if (e != TEVO_EUNSUPPORTED) return e;
+  }
   // G2: T_p[(s v), b] = Wg[(s v), (w s')] X_p[(w s'), b]
   TRY(gemm(s, gd(Wg, 0, (long long)k.wl * k.d, 1, s->X.p, (long long)k.wl * k.d * k.Db, k.Db, 1, s->T.p,
                  (long long)k.d * k.wr * k.Db, k.Db, 1, k.d * k.wr, k.Db, k.wl * k.d, k.Dp)));
@@ -287,7 +298,7 @@ int sweep64(tevo_mps s, tevo_mpo W) {
   const int d = s->d;
   for (int i = 0; i + 1 < s->L; ++i) {
     StepDims k = right_dims(s, W, i);
-    TRY(make_T64(s, k, env_slot(s, i), zp(s->A[i]), zp(W->Wr[i])));
+    TRY(make_T64(s, k, env_slot(s, i), zp(s->A[i]), zp(W->Wr[i]), &W->Sr_idx[i], &W->Sr_val[i]));
     TRY(apply64(s, k, env_slot(s, i + 1), zp(s->Bq)));
     TRY(qr_q(s, k.Dp * d, k.Dq, false));
     TRY(store_right(s, zp(s->Bq), zp(s->Anew[i]), k.Dp, d, k.Dq));
@@ -296,7 +307,7 @@ int sweep64(tevo_mps s, tevo_mpo W) {
   for (int i = s->L - 1; i >= 1; --i) {
     StepDims k = left_dims(s, W, i);
     TRY(mirror_site64(L, zp(s->A[i]), zp(s->Atmp), s->dims[i], d, s->dims[i + 1]));
-    TRY(make_T64(s, k, env_slot(s, i + 1), zp(s->Atmp), zp(W->Wl[i])));
+    TRY(make_T64(s, k, env_slot(s, i + 1), zp(s->Atmp), zp(W->Wl[i]), &W->Sl_idx[i], &W->Sl_val[i]));
     TRY(apply64(s, k, env_slot(s, i), zp(s->Bq)));
     TRY(qr_q(s, k.Dp * d, k.Dq, false));
     TRY(store_left(s, zp(s->Bq), zp(s->Anew[i]), k.Dq, d, k.Dp));
@@ -312,7 +323,7 @@ int build_right_envs64(tevo_mps s, tevo_mpo W, std::vector<Buf>& bra, std::vecto
   for (int i = s->L - 1; i >= 1; --i) {
     StepDims k = left_dims(s, W, i);
     TRY(mirror_site64(L, zp(ket[i]), zp(s->Atmp), s->dims[i], d, s->dims[i + 1]));
-    TRY(make_T64(s, k, env_slot(s, i + 1), zp(s->Atmp), zp(W->Wl[i])));
+    TRY(make_T64(s, k, env_slot(s, i + 1), zp(s->Atmp), zp(W->Wl[i]), &W->Sl_idx[i], &W->Sl_val[i]));
     // bra^T as a column-major (Dr d) x Dl matrix
     TRY(mirror_site64(L, zp(bra[i]), zp(s->Atmp), s->dims[i], d, s->dims[i + 1]));
     TRY(copy2d64(L, zp(s->Atmp), k.Dq, 1, zp(s->Bq), 1, k.Dp * d, k.Dp * d, k.Dq));
@@ -326,7 +337,7 @@ int centre64(tevo_mps s, tevo_mpo W) {
   const int d = s->d;
   StepDims k = left_dims(s, W, 0);
   TRY(mirror_site64(L, zp(s->A[0]), zp(s->Atmp), s->dims[0], d, s->dims[1]));
-  TRY(make_T64(s, k, env_slot(s, 1), zp(s->Atmp), zp(W->Wl[0])));
+  TRY(make_T64(s, k, env_slot(s, 1), zp(s->Atmp), zp(W->Wl[0]), &W->Sl_idx[0], &W->Sl_val[0]));
   TRY(apply64(s, k, env_slot(s, 0), zp(s->Bq)));
   TRY(store_left(s, zp(s->Bq), zp(s->Anew[0]), k.Dq, d, k.Dp));
   return 0;
@@ -499,6 +510,10 @@ extern "C" int mpo_build(tevo_ctx c, int L, int d, int chi, const double* A, con
   W->W.resize(L);
   W->Wr.resize(L);
   W->Wl.resize(L);
+  W->Sr_idx.resize(L);
+  W->Sr_val.resize(L);
+  W->Sl_idx.resize(L);
+  W->Sl_val.resize(L);
   for (int i = 0; i < L; ++i) {
     const int wl = W->wl[i], wr = W->wr[i];
     const auto& S = W->host[i];
@@ -512,7 +527,41 @@ extern "C" int mpo_build(tevo_ctx c, int L, int d, int chi, const double* A, con
             gl[((size_t)s * wl + a) * (wr * d) + (size_t)b * d + t] = v;  // [(s wl)][(wr s')]
           }
     const size_t bytes = sizeof(z64) * S.size();
-    int e = dalloc(c, W->W[i], bytes);
+    // CSR of the two G2 operands: rows d*wr (d*wl), columns wl*d (wr*d)
+    auto csr = [&](const std::vector<std::complex<double>>& g, int rows, int cols, Buf& bidx, Buf& bval) -> int {
+      std::vector<int> idx(1, 0);
+      std::vector<std::complex<double>> val;
+      std::vector<int> cidx;
+      for (int r = 0; r < rows; ++r) {
+        for (int q = 0; q < cols; ++q) {
+          auto v = g[(size_t)r * cols + q];
+          if (v != std::complex<double>(0.0, 0.0)) {
+            cidx.push_back(q);
+            val.push_back(v);
+          }
+        }
+        idx.push_back((int)cidx.size());
+      }
+      idx.insert(idx.end(), cidx.begin(), cidx.end());
+      if (val.empty()) val.push_back(0.0);
+      int e = dalloc(c, bidx, sizeof(int) * idx.size());
+      if (!e) e = dalloc(c, bval, sizeof(z64) * val.size());
+      if (e) return e;
+      if (cudaMemcpyAsync(bidx.p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, c->stream) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(bval.p, val.data(), sizeof(z64) * val.size(), cudaMemcpyHostToDevice, c->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return TEVO_ECUDA;
+      return 0;
+    };
+    int e = csr(gr, d * wr, wl * d, W->Sr_idx[i], W->Sr_val[i]);
+    if (!e) e = csr(gl, d * wl, wr * d, W->Sl_idx[i], W->Sl_val[i]);
+    if (e) {
+      mpo_destroy(W);
+      return e;
+    }
+    e = dalloc(c, W->W[i], bytes);
     if (!e) e = dalloc(c, W->Wr[i], bytes);
     if (!e) e = dalloc(c, W->Wl[i], bytes);
     if (e) {
@@ -577,6 +626,8 @@ extern "C" int mpo_destroy(tevo_mpo W) {
   for (auto& b : W->W) dfree(W->ctx, b);
   for (auto& b : W->Wr) dfree(W->ctx, b);
   for (auto& b : W->Wl) dfree(W->ctx, b);
+  for (auto* v : {&W->Sr_idx, &W->Sr_val, &W->Sl_idx, &W->Sl_val})
+    for (auto& b : *v) dfree(W->ctx, b);
   mixed_mpo_destroy(W->ctx, W->mixed);
   delete W;
   return 0;

@@ -224,6 +224,69 @@ int zgemm64(const Launch& L, const GemmDesc& g, void* workspace, size_t ws_bytes
 }
 
 // ---------------------------------------------------------------------------
+// G2 with the MPO's zero entries skipped
+// ---------------------------------------------------------------------------
+namespace {
+
+// T_p[r][b] = sum over the nonzeros (r, k) of W: W[r][k] * X_p[k][b].
+// One CTA per (p, block of BW columns b): X_p[:, block] is staged in shared
+// memory; a warp walks the nonzeros of one row r for 32 consecutive b.
+// The nonzeros of a row are visited in increasing k, the order in which the
+// dense kernel accumulates them, and skipped entries are exact zeros, so the
+// result equals the dense contraction bit for bit.
+__global__ void __launch_bounds__(256) zsparse_g2_kernel(const double2* __restrict__ X, double2* __restrict__ T,
+                                                         const int* __restrict__ row_ptr,
+                                                         const int* __restrict__ col_idx,
+                                                         const double2* __restrict__ vals, int R, int K, int Db,
+                                                         int BW) {
+  extern __shared__ double2 xs[];  // [K][BW]
+  const int p = blockIdx.y;
+  const int b0 = blockIdx.x * BW;
+  const int bw = min(BW, Db - b0);
+  const double2* Xp = X + (long long)p * K * Db;
+  for (int idx = threadIdx.x; idx < K * BW; idx += blockDim.x) {
+    const int k = idx / BW, bb = idx % BW;
+    xs[idx] = (bb < bw) ? Xp[(long long)k * Db + b0 + bb] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  double2* Tp = T + (long long)p * R * Db;
+  const int lanes = min(BW, 32);
+  const int per_block = blockDim.x / lanes;  // rows processed at once
+  const int bb = threadIdx.x % lanes, rsub = threadIdx.x / lanes;
+  for (int r = rsub; r < R; r += per_block) {
+    for (int bc = bb; bc < bw; bc += lanes) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) acc = cfma(vals[e], xs[col_idx[e] * BW + bc], acc);
+      Tp[(long long)r * Db + b0 + bc] = acc;
+    }
+  }
+}
+
+}  // namespace
+
+int zsparse_g2(const Launch& L, const z64* X, z64* T, const int* row_ptr, const int* col_idx, const z64* vals,
+               int R, int K, int Db, int batch) {
+  int BW = 32;
+  while (BW > 8 && (size_t)K * BW * sizeof(double2) > 200 * 1024) BW /= 2;
+  const size_t smem = (size_t)K * BW * sizeof(double2);
+  if (smem > 220 * 1024) return TEVO_EUNSUPPORTED;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(zsparse_g2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) !=
+        cudaSuccess)
+      return TEVO_ECUDA;
+    attr = true;
+  }
+  if (batch > 65535) return TEVO_ESHAPE;
+  dim3 grid((Db + BW - 1) / BW, batch);
+  zsparse_g2_kernel<<<grid, 256, smem, L.stream>>>(reinterpret_cast<const double2*>(X), reinterpret_cast<double2*>(T),
+                                                    row_ptr, col_idx, reinterpret_cast<const double2*>(vals), R, K,
+                                                    Db, BW);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
 // Householder QR
 // ---------------------------------------------------------------------------
 namespace {

@@ -77,6 +77,11 @@ struct Launch {
 size_t zgemm64_workspace(const GemmDesc& g, int num_sms);
 int zgemm64(const Launch& L, const GemmDesc& g, void* workspace, size_t ws_bytes);
 
+// G2 over the nonzeros of the MPO operand (CSR rows of [(s v)][(wl s')]):
+// T[p][r][b] = sum_k W[r][k] X[p][k][b], batch p, R rows, K = wl d, Db columns
+int zsparse_g2(const Launch& L, const z64* X, z64* T, const int* row_ptr, const int* col_idx, const z64* vals,
+               int R, int K, int Db, int batch);
+
 // Householder QR of a column-major m x n matrix (ld = m), in place.
 // V (m x n col-major) receives the reflectors, tau/beta (n) the scalars.
 // scratch: >= qr64_scratch_bytes(m, n).
