@@ -122,6 +122,9 @@ struct tevo_mps_s {
   // workspace of evolve_step
   std::vector<size_t> env_off;
   Buf env, X, T, Bq, V, tau, beta, Atmp, Rm, gemm_ws, red;
+  Buf qrflags;        // [0] error flag of the cooperative QR, [1..] reflector flags
+  int qr_epoch = 0;
+  bool coop_qr = true;  // off while a batched step issues (concurrent streams, graph capture)
   int wmax = 0;
   MixedState* mixed = nullptr;
 };
@@ -208,7 +211,15 @@ int env64(tevo_mps s, const StepDims& k, const z64* Qc, z64* Enew) {
 // QR of the column-major Bq (m x n) and explicit Q written back into Bq
 int qr_q(tevo_mps s, int m, int n, bool keep_r) {
   Launch L = launch_of(s->ctx);
-  TRY(qr64_factor(L, zp(s->Bq), m, n, zp(s->V), zp(s->tau), zp(s->beta), static_cast<double*>(s->red.p)));
+  int* qf = static_cast<int*>(s->qrflags.p);
+  int e = TEVO_EUNSUPPORTED;
+  if (qf && s->coop_qr) {
+    s->qr_epoch = s->qr_epoch == 0x3fffffff ? 1 : s->qr_epoch + 1;
+    e = qr64_factor_coop(L, zp(s->Bq), m, n, zp(s->V), zp(s->tau), zp(s->beta), s->red.p, qf + 1, s->qr_epoch, qf);
+  }
+  if (e == TEVO_EUNSUPPORTED)
+    e = qr64_factor(L, zp(s->Bq), m, n, zp(s->V), zp(s->tau), zp(s->beta), static_cast<double*>(s->red.p));
+  TRY(e);
   if (keep_r) TRY(qr64_extract_r(L, zp(s->Bq), zp(s->beta), m, n, zp(s->Rm)));
   return qr64_form_q(L, zp(s->V), zp(s->tau), m, n, zp(s->Bq), 1, m);
 }
@@ -261,6 +272,11 @@ int workspace(tevo_mps s, tevo_mpo W) {
   TRY(ensure(c, s->Rm, sizeof(z64) * (size_t)s->D * s->D + 64));
   TRY(ensure(c, s->gemm_ws, (size_t)48 << 20));
   TRY(ensure(c, s->red, sizeof(double) * 4096));
+  if (!s->qrflags.p) {
+    TRY(ensure(c, s->qrflags, sizeof(int) * ((size_t)s->D * d + 64)));
+    TRYCUDA(cudaMemsetAsync(s->qrflags.p, 0, s->qrflags.bytes, c->stream));
+    s->qr_epoch = 0;
+  }
   return 0;
 }
 
@@ -718,7 +734,7 @@ extern "C" int mps_destroy(tevo_mps s) {
   for (auto& b : s->A) dfree(c, b);
   for (auto& b : s->Anew) dfree(c, b);
   for (Buf* b : {&s->scalars, &s->env, &s->X, &s->T, &s->Bq, &s->V, &s->tau, &s->beta, &s->Atmp, &s->Rm,
-                 &s->gemm_ws, &s->red})
+                 &s->gemm_ws, &s->red, &s->qrflags})
     dfree(c, *b);
   mixed_state_destroy(c, s->mixed);
   delete s;
@@ -789,11 +805,13 @@ int evolve_issue(tevo_mps s, tevo_mpo W, int sweeps, int precision, bool* mixed_
 // device flags of the step just issued (synchronises the context stream)
 int evolve_check(tevo_mps s, bool mixed) {
   tevo_ctx c = s->ctx;
-  int flag = 0, tflag = 0;
+  int flag = 0, tflag = 0, qflag = 0;
   TRYCUDA(cudaMemcpyAsync(&flag, scal(s, 4), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  if (s->qrflags.p)
+    TRYCUDA(cudaMemcpyAsync(&qflag, s->qrflags.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   if (mixed) TRY(mixed_error_flag(c, s, &tflag));
   TRYCUDA(cudaStreamSynchronize(c->stream));
-  if (tflag) return TEVO_ETIMEOUT;
+  if (tflag || qflag) return TEVO_ETIMEOUT;
   if (flag) return TEVO_ENONFINITE;
   return 0;
 }
@@ -875,8 +893,10 @@ int batch_issue(BatchPlan* p, cudaStream_t origin) {
     tevo_mps s = p->psis[c];
     cudaStream_t saved = s->ctx->stream;
     s->ctx->stream = p->streams[j % p->nstreams];
+    s->coop_qr = false;
     bool mixed = false;
     int e = evolve_issue(s, p->Ws[c], p->sweeps, p->precision, &mixed);
+    s->coop_qr = true;
     s->ctx->stream = saved;
     if (e) return e;
     p->mixed = mixed;

@@ -7,6 +7,7 @@
 // per CTA in registers and splits K until every SM has work.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -421,6 +422,168 @@ __global__ void qr_form_q_kernel(const double2* V, const double2* tau, int m, in
   for (int r = threadIdx.x; r < m; r += blockDim.x) Q[(long long)r * sQr + (long long)c * sQc] = q[r];
 }
 
+// Cooperative Householder factorisation, one launch for all columns. CTA c owns
+// columns j = c, c + G, c + 2G, ... (G = grid size), kept in shared memory. At
+// step k the owner of column k publishes reflector k (V[:, k], tau[k], beta[k],
+// then a release flag), every other CTA acquires it and applies H_k^H to its own
+// columns > k. The owner of column k + 1 updates that column first and publishes
+// reflector k + 1 before updating its other columns, so the chain of dependent
+// work per step is one column update plus one norm. All CTAs are co-resident
+// (cooperative launch); every wait is bounded (err, code 8) and, after a
+// timeout, all CTAs leave.
+constexpr unsigned long long QR_WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long qr_gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// reflector of the column x[k..m) (in shared memory) into vout[k..m); returns
+// tau, writes beta; deflation as in qr_step_kernel
+__device__ void make_reflector(const double2* x, double2* vout, int k, int m, double tol, double2* tau_out,
+                               double2* beta_out, double* red) {
+  double s = 0.0;
+  for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
+    double2 a = x[r];
+    s = fma(a.x, a.x, s);
+    s = fma(a.y, a.y, s);
+  }
+  const double nrm = sqrt(block_sum(s, red));
+  const double2 alpha = x[k];
+  const bool deflate = (nrm <= tol) || (nrm == 0.0);
+  if (deflate) {
+    for (int r = k + threadIdx.x; r < m; r += blockDim.x) vout[r] = make_double2(r == k ? 1.0 : 0.0, 0.0);
+    *tau_out = make_double2(0.0, 0.0);
+    *beta_out = alpha;
+    return;
+  }
+  const double b = alpha.x >= 0.0 ? -nrm : nrm;
+  const double2 den = make_double2(alpha.x - b, alpha.y);
+  const double dd = den.x * den.x + den.y * den.y;
+  const double2 inv = make_double2(den.x / dd, -den.y / dd);
+  for (int r = k + threadIdx.x; r < m; r += blockDim.x) vout[r] = (r == k) ? make_double2(1.0, 0.0) : cmul(x[r], inv);
+  *tau_out = make_double2((b - alpha.x) / b, -alpha.y / b);
+  *beta_out = make_double2(b, 0.0);
+}
+
+// col[k..m) -= conj(tau) v (v^H col[k..m))
+__device__ void apply_reflector(double2* col, const double2* v, double2 tau, int k, int m, double* red) {
+  if (tau.x == 0.0 && tau.y == 0.0) return;  // uniform across the block
+  double2 w = make_double2(0.0, 0.0);
+  for (int r = k + threadIdx.x; r < m; r += blockDim.x) w = cfma(cconj(v[r]), col[r], w);
+  w = block_csum(w, red);
+  const double2 f = cmul(cconj(tau), w);
+  for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
+    double2 d = cmul(v[r], f);
+    col[r] = make_double2(col[r].x - d.x, col[r].y - d.y);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, double2* V, double2* tau,
+                                                      double2* beta, const double* frob2, int* flags, int epoch,
+                                                      int* err) {
+  extern __shared__ double2 sm[];
+  __shared__ double red[64];
+  __shared__ double2 s_tau[2], s_beta;
+  __shared__ int s_abort;
+  const int G = gridDim.x, c = blockIdx.x;
+  const int ncols = (n - c + G - 1) / G;  // columns owned
+  double2* cols = sm;                      // [ncols][m]
+  double2* vb[2] = {sm + (size_t)ncols * m, sm + (size_t)(ncols + 1) * m};
+  const double tol = DEFLATE * sqrt(*frob2);
+  for (int jj = 0; jj < ncols; ++jj) {
+    const int j = c + jj * G;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) cols[(size_t)jj * m + r] = A[(long long)j * m + r];
+  }
+  if (threadIdx.x == 0) s_abort = 0;
+  __syncthreads();
+  // publish reflector k held in vb[k & 1] (called by the owner of column k)
+  auto publish = [&](int k) {
+    const double2* v = vb[k & 1];
+    double2* Vk = V + (long long)k * m;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) Vk[r] = (r < k) ? make_double2(0.0, 0.0) : v[r];
+    // the R part of column k (rows above k) for qr64_extract_r
+    const double2* col = cols + (size_t)(k / G) * m;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) A[(long long)k * m + r] = col[r];
+    __threadfence();  // each thread's stores, before the release below
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tau[k] = s_tau[k & 1];
+      beta[k] = s_beta;
+      __threadfence();
+      st_release(flags + k, epoch);
+    }
+  };
+  // the owner of column 0 starts the chain
+  if (c == 0) {
+    double2 t, b;
+    make_reflector(cols, vb[0], 0, m, tol, &t, &b, red);
+    if (threadIdx.x == 0) {
+      s_tau[0] = t;
+      s_beta = b;
+    }
+    __syncthreads();
+    publish(0);
+  }
+  for (int k = 0; k < n; ++k) {
+    const int owner = k % G;
+    double2* v = vb[k & 1];
+    if (owner != c) {
+      // acquire reflector k
+      if (threadIdx.x == 0) {
+        if (ld_acquire(flags + k) != epoch) {
+          const unsigned long long t0 = qr_gtimer();
+          while (ld_acquire(flags + k) != epoch) {
+            if (qr_gtimer() - t0 > QR_WAIT_NS) {
+              atomicExch(err, 8);
+              s_abort = 1;
+              break;
+            }
+          }
+        }
+        if (!s_abort) s_tau[k & 1] = __ldcg(tau + k);
+      }
+      __syncthreads();
+      if (s_abort) return;
+      const double2* Vk = V + (long long)k * m;
+      for (int r = k + threadIdx.x; r < m; r += blockDim.x) v[r] = __ldcg(Vk + r);  // L2, never a stale L1 line
+      __syncthreads();
+    }
+    const double2 t = s_tau[k & 1];
+    // look-ahead: column k + 1 first, then publish reflector k + 1
+    const int k1 = k + 1;
+    if (k1 < n && (k1 % G) == c) {
+      double2* col = cols + (size_t)(k1 / G) * m;
+      apply_reflector(col, v, t, k, m, red);
+      double2 t1, b1;
+      make_reflector(col, vb[k1 & 1], k1, m, tol, &t1, &b1, red);
+      if (threadIdx.x == 0) {
+        s_tau[k1 & 1] = t1;
+        s_beta = b1;
+      }
+      __syncthreads();
+      publish(k1);
+    }
+    for (int jj = 0; jj < ncols; ++jj) {
+      const int j = c + jj * G;
+      if (j <= k || j == k1) continue;
+      apply_reflector(cols + (size_t)jj * m, v, t, k, m, red);
+    }
+  }
+}
+
 __global__ void qr_extract_r_kernel(const double2* A, const double2* beta, int m, int n, double2* R) {
   long long total = (long long)n * n;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -469,6 +632,42 @@ int qr64_factor(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_, z64*
   }
   if (L.prof) L.prof->end(L.stream, pr);
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int qr64_factor_coop(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_, z64* beta_, void* scratch,
+                     int* flags, int epoch, int* err) {
+  if (m < n || n <= 0) return TEVO_ESHAPE;
+  double2* A = reinterpret_cast<double2*>(A_);
+  double* part = reinterpret_cast<double*>(scratch);
+  double* frob2 = part + FROB_BLOCKS;
+  const int G = std::min(n, L.num_sms);
+  const int ncols = (n + G - 1) / G;
+  const size_t smem = sizeof(double2) * (size_t)(ncols + 2) * m;
+  if (smem > 200 * 1024) return TEVO_EUNSUPPORTED;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(qr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+      return TEVO_ECUDA;
+    attr = true;
+  }
+  // every CTA must be resident at once: check the occupancy for this size
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_coop_kernel, 256, smem) != cudaSuccess ||
+      per_sm * L.num_sms < G)
+    return TEVO_EUNSUPPORTED;
+  const double qflops = 8.0 * (4.0 * (double)m * n * n - 4.0 / 3.0 * (double)n * n * n);
+  int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_QR, qflops, 32.0 * (double)m * n) : -1;
+  frob_partial_kernel<<<FROB_BLOCKS, 256, 0, L.stream>>>(A, (long long)m * n, part);
+  sum_partials_kernel<<<1, 256, 0, L.stream>>>(part, FROB_BLOCKS, frob2);
+  *L.launches += 2;
+  double2* V = reinterpret_cast<double2*>(V_);
+  double2* tau = reinterpret_cast<double2*>(tau_);
+  double2* beta = reinterpret_cast<double2*>(beta_);
+  void* args[] = {&A, &m, &n, &V, &tau, &beta, &frob2, &flags, &epoch, &err};
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)qr_coop_kernel, dim3(G), dim3(256), args, smem, L.stream);
+  ++*L.launches;
+  if (L.prof) L.prof->end(L.stream, pr);
+  return e == cudaSuccess ? 0 : TEVO_ECUDA;
 }
 
 int qr64_form_q(const Launch& L, const z64* V, const z64* tau, int m, int n, z64* Q, long long sQr,

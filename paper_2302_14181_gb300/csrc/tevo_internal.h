@@ -87,6 +87,11 @@ int zsparse_g2(const Launch& L, const z64* X, z64* T, const int* row_ptr, const 
 // scratch: >= qr64_scratch_bytes(m, n).
 size_t qr64_scratch_bytes(int m, int n);
 int qr64_factor(const Launch& L, z64* A, int m, int n, z64* V, z64* tau, z64* beta, void* scratch);
+// the same factorisation as one cooperative launch (columns owned by CTAs, the
+// reflectors passed through V with release/acquire flags[k] = epoch); returns
+// TEVO_EUNSUPPORTED when the matrix does not fit (then use qr64_factor)
+int qr64_factor_coop(const Launch& L, z64* A, int m, int n, z64* V, z64* tau, z64* beta, void* scratch, int* flags,
+                     int epoch, int* err);
 // explicit thin Q (m x n) written with element (r, c) at Q[r * sQr + c * sQc]
 int qr64_form_q(const Launch& L, const z64* V, const z64* tau, int m, int n, z64* Q, long long sQr,
                 long long sQc);
