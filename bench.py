@@ -170,6 +170,13 @@ def oracle_sample(cfg, seconds=15.0, seed=7):
             "t_step_s": t_step}
 
 
+def config_of(cfg, sweeps, precision, world=1):
+    return {"workload": WORKLOAD, "model": "long-range Ising, J(r)=sum_k a_k b_k^r ~ 1/r^2, g=0.7",
+            "L": cfg["L"], "D": cfg["D"], "N": cfg["N"], "w": 93, "tau": "-0.2i", "sweeps": sweeps,
+            "precision": precision, "l2": "inputs larger than L2 (environments ~9.7 GB)",
+            "parallelism": f"replicas x{world}"}
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -188,8 +195,7 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "sweeps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "L": cfg["L"], "D": cfg["D"], "N": cfg["N"],
-                                        "sweeps": cfg["sweeps"], "precision": "fp64 oracle (numpy, host)"},
+        "data": "synthetic", "config": config_of(cfg, cfg["sweeps"], "fp64 oracle (numpy, host cores)"),
         "cpu_baseline": {"value": v, "unit": "sweeps/s", "cores": s["cores"], "kind": "oracle",
                          "sample": "10 s of oracle local updates (make_T, apply, Householder QR, environment) "
                                    "per step at the interior-site shape D=256, w=93, d=2, scaled to one "
@@ -372,10 +378,7 @@ def our_arm(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "c128" if prec == 0 else f"{args.precision} contractions + c128 QR/final sweep",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "model": "long-range Ising, J(r)=sum_k a_k b_k^r ~ 1/r^2, g=0.7",
-                       "L": cfg["L"], "D": D, "N": cfg["N"], "w": max(wd), "tau": "-0.2i", "sweeps": sweeps,
-                       "precision": args.precision, "l2": "inputs larger than L2 (environments ~9.7 GB)",
-                       "parallelism": f"replicas x{world}"},
+            "config": config_of(cfg, sweeps, args.precision, world),
             "tflops": flops * args.steps * world / (ms_max / 1e3) / 1e12,
             "roofline": roof,
             "roofline_other": {k: roofs[k] for k in other},

@@ -299,3 +299,20 @@ def test_site_dependent_couplings_match_dense():
         U = dense.mpo_to_dense(mpo.build_mpo(*blocks, 2, -1j * t))
         errs.append(np.linalg.norm(U - dense.expm_tau_h(H, -1j * t), 2))
     assert np.log2(errs[0] / errs[1]) > 2.75
+
+
+@pytest.mark.parametrize("variant", [mpo.FULL, mpo.PLAIN])
+def test_complex_step_splitting_is_second_order(variant):
+    """Sec. 7.3: two first-order operators at the complex steps tau (1 + i)/2 and
+    tau (1 - i)/2 compose to a second-order approximation of exp(tau H): the
+    error falls by 2^3 when tau halves."""
+    L = 6
+    blocks = wl.xxz_blocks(L, 0.5)
+    H = dense.hamiltonian_from_blocks(*blocks)
+    errs = []
+    for t in (0.2, 0.1, 0.05):
+        tau = -1j * t
+        U1 = dense.mpo_to_dense(mpo.build_mpo(*blocks, 1, tau * (1 + 1j) / 2, variant))
+        U2 = dense.mpo_to_dense(mpo.build_mpo(*blocks, 1, tau * (1 - 1j) / 2, variant))
+        errs.append(np.linalg.norm(U2 @ U1 - dense.expm_tau_h(H, tau), 2))
+    assert np.log2(errs[0] / errs[1]) > 2.9 and np.log2(errs[1] / errs[2]) > 2.9
