@@ -149,11 +149,13 @@ int mps_destroy(tevo_mps psi);
  * the cap psi was created with (TEVO_ESHAPE otherwise). precision is one of
  * TEVO_FP64 / TF32 / TF32X3 / BF16X3: for the low-precision forms the first
  * sweeps-1 sweeps use tensor-core contractions and the last sweep (preceded by
- * a rebuild of the right environments) is fp64; the QR, the norm and every
- * reduction are fp64 in all forms.
+ * a rebuild of the right environments) is fp64 (with sweeps = 1 the step is all
+ * fp64); OR-ing TEVO_TC_ONLY makes every sweep a tensor-core sweep. The QR, the
+ * norm and every reduction are fp64 in all forms.
  * Errors: TEVO_EINVAL, TEVO_ESHAPE, TEVO_ETAU, TEVO_ENOMEM, TEVO_ECUDA,
- * TEVO_ENONFINITE (norm of the fitted state is 0, NaN or Inf),
- * TEVO_EUNSUPPORTED. Asynchronous on the context stream.
+ * TEVO_ENONFINITE (norm of the fitted state is 0, NaN or Inf), TEVO_ETIMEOUT
+ * (a bounded device wait gave up), TEVO_EUNSUPPORTED. The work is issued on
+ * the context stream; the call then synchronises to read the device status flags.
  */
 int evolve_step(tevo_mps psi, tevo_mpo W, double tau_re, double tau_im, int D, int sweeps,
                 int precision);

@@ -271,7 +271,33 @@ __global__ void transpose_planes_kernel(TcTranspose t) {
   }
 }
 
-template <int KIND>
+// product tables (compile-time): A plane, B plane, accumulator (0 = Re, 1 = Im),
+// negate-A flag, and whether the product is the first into its accumulator
+template <int NPROD>
+struct Prod;
+template <>
+struct Prod<12> {  // split forms: planes re_hi, re_lo, im_hi, im_lo; hi.hi + hi.lo + lo.hi
+  // products 0-5 accumulate Re (Ar.Br terms, then -Ai.Bi terms), 6-11 Im (Ar.Bi, then Ai.Br)
+  __host__ __device__ static constexpr int a(int p) {
+    return (p % 6) < 2 ? 0 : (p % 6) == 2 ? 1 : (p % 6) < 5 ? 2 : 3;  // hi hi lo | hi hi lo
+  }
+  __host__ __device__ static constexpr int b(int p) {
+    return p < 3 ? (p == 1 ? 1 : 0) : p < 6 ? (p == 4 ? 3 : 2) : p < 9 ? (p == 7 ? 3 : 2) : (p == 10 ? 1 : 0);
+  }
+  __host__ __device__ static constexpr int acc(int p) { return p < 6 ? 0 : 1; }
+  __host__ __device__ static constexpr bool neg(int p) { return p >= 3 && p < 6; }
+  __host__ __device__ static constexpr bool first(int p) { return p == 0 || p == 6; }
+};
+template <>
+struct Prod<4> {  // plain tf32: planes re, im
+  __host__ __device__ static constexpr int a(int p) { return p == 1 || p == 3 ? 1 : 0; }
+  __host__ __device__ static constexpr int b(int p) { return p == 1 || p == 2 ? 1 : 0; }
+  __host__ __device__ static constexpr int acc(int p) { return p < 2 ? 0 : 1; }
+  __host__ __device__ static constexpr bool neg(int p) { return p == 1; }
+  __host__ __device__ static constexpr bool first(int p) { return p == 0 || p == 2; }
+};
+
+template <int KIND, int NPROD>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -365,7 +391,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (!mbar_wait(tempty0 + 8 * b, (uint32_t(i >> 1) & 1u) ^ 1u, a.err, 5)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dbase = tmem + (uint32_t)(b * 2 * TN);
-        bool started[2] = {false, false};
         for (int kt = kt0; kt < kt1; ++kt, ++g) {
           const int s = int(g % NSTAGE);
           const uint32_t ph = uint32_t(g / NSTAGE) & 1u;
@@ -375,15 +400,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
+          // descriptors of plane 0 of this stage; planes and K-steps are fixed offsets
+          const uint64_t ad0 = sdesc(sa), bd0 = sdesc(sb);
 #pragma unroll
           for (int ks = 0; ks < KCB / 32; ++ks) {
-            for (int p = 0; p < a.nprod; ++p) {
-              const uint64_t ad = sdesc(sa + a.a_plane[p] * TM * KCB + ks * 32);
-              const uint64_t bd = sdesc(sb + a.b_plane[p] * TN * KCB + ks * 32);
-              const int acc = a.acc[p];
-              const uint32_t id = base_id | (a.neg[p] ? (1u << 13) : 0u);
-              mma<KIND>(dbase + acc * TN, ad, bd, id, started[acc] ? 1u : 0u);
-              started[acc] = true;
+#pragma unroll
+            for (int p = 0; p < NPROD; ++p) {
+              const uint64_t ad = ad0 + (uint64_t)((Prod<NPROD>::a(p) * TM * KCB + ks * 32) >> 4);
+              const uint64_t bd = bd0 + (uint64_t)((Prod<NPROD>::b(p) * TN * KCB + ks * 32) >> 4);
+              const uint32_t id = base_id | (Prod<NPROD>::neg(p) ? (1u << 13) : 0u);
+              const bool first = (kt == kt0) && ks == 0 && Prod<NPROD>::first(p);
+              mma<KIND>(dbase + Prod<NPROD>::acc(p) * TN, ad, bd, id, first ? 0u : 1u);
             }
           }
           mma_commit(empty0 + 8 * s);
@@ -575,13 +602,15 @@ void tc_products(int fmt, TcArgs& a) {
 }
 
 int tc_gemm(const Launch& L, int fmt, const TcOperand& A, const TcOperand& B, int M, int N, TcArgs args) {
-  static bool attr_done[2] = {false, false};
-  const int kind = fmt == TC_BF16 ? 0 : 1;
+  static bool attr_done[3] = {false, false, false};
+  const int kind = fmt == TC_BF16 ? 0 : (fmt == TC_TF32X3 ? 1 : 2);
   if (!attr_done[kind]) {
-    cudaError_t e = kind == 0 ? cudaFuncSetAttribute(tc_gemm_kernel<TC_BF16>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
-                              : cudaFuncSetAttribute(tc_gemm_kernel<TC_TF32>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = kind == 0   ? cudaFuncSetAttribute(tc_gemm_kernel<TC_BF16, 12>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
+                    : kind == 1 ? cudaFuncSetAttribute(tc_gemm_kernel<TC_TF32, 12>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
+                                : cudaFuncSetAttribute(tc_gemm_kernel<TC_TF32, 4>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return TEVO_ECUDA;
     attr_done[kind] = true;
   }
@@ -615,9 +644,11 @@ int tc_gemm(const Launch& L, int fmt, const TcOperand& A, const TcOperand& B, in
                                   (double)A.elem_bytes * A.planes * ((double)M + N) * A.k_in * A.k_out)
                   : -1;
   if (kind == 0)
-    tc_gemm_kernel<TC_BF16><<<grid, TC_THREADS, SMEM_BYTES, L.stream>>>(ma, mb, args);
+    tc_gemm_kernel<TC_BF16, 12><<<grid, TC_THREADS, SMEM_BYTES, L.stream>>>(ma, mb, args);
+  else if (kind == 1)
+    tc_gemm_kernel<TC_TF32, 12><<<grid, TC_THREADS, SMEM_BYTES, L.stream>>>(ma, mb, args);
   else
-    tc_gemm_kernel<TC_TF32><<<grid, TC_THREADS, SMEM_BYTES, L.stream>>>(ma, mb, args);
+    tc_gemm_kernel<TC_TF32, 4><<<grid, TC_THREADS, SMEM_BYTES, L.stream>>>(ma, mb, args);
   ++*L.launches;
   if (L.prof) L.prof->end(L.stream, pr);
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
