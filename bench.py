@@ -8,7 +8,7 @@ method is quoted on for this build. The state lives in HBM across steps; the
 environments (about 9.7 GB in fp64) are larger than L2, so no flush is needed.
 
 Usage:
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16x3|tf32x3|tf32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16x3|tf32x3|tf32|bf16x3+oz|...]
   python bench.py --impl reference ...     # the fp64 oracle on the host cores
 Prints one JSON line (rank 0).
 """
@@ -34,7 +34,11 @@ import workloads as wl  # noqa: E402
 METRIC = "W^(N)·MPS fit sweeps/s & TFLOP/s vs peak at ≤1e-6 obs error, mixed vs FP64"
 WORKLOAD = "lri_L100_N3_D256"
 PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3,
-        "tc-tf32": 0x101, "tc-tf32x3": 0x102, "tc-bf16x3": 0x103}
+        "tc-tf32": 0x101, "tc-tf32x3": 0x102, "tc-bf16x3": 0x103,
+        # fp64 contractions as Ozaki-scheme GEMMs (7 digit slices) on the tensor cores
+        "fp64+oz": 0x200, "tf32+oz": 0x201, "tf32x3+oz": 0x202, "bf16x3+oz": 0x203}
+OZ_SLICES = 7
+OZ_PAIRS = OZ_SLICES * (OZ_SLICES + 1) // 2  # digit-slice products per complex product
 # fp64 issue rate on GB300: 2 DFMA per clock per SM (152 SMs, 2070 MHz max SM clock)
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 
@@ -170,6 +174,23 @@ def oracle_sample(cfg, seconds=15.0, seed=7):
             "t_step_s": t_step}
 
 
+NPROF = 6
+PROF_NAMES = ["gemm64", "gemm_tc", "qr", "form_q", "gemm_oz", "oz_split"]
+
+
+def dtype_of(form):
+    if form == "fp64":
+        return "c128"
+    if form == "fp64+oz":
+        return "c128 in/out; contractions as exact bf16 digit-slice products (Ozaki, 7 slices), fp64 sums"
+    base = form.replace("tc-", "").replace("+oz", "")
+    if form.startswith("tc-"):
+        return f"{base} contractions + c128 QR"
+    if form.endswith("+oz"):
+        return f"{base} contractions + c128 QR; fp64 rebuild/final sweep as Ozaki bf16 digit-slice GEMMs"
+    return f"{base} contractions + c128 QR/final sweep"
+
+
 def config_of(cfg, sweeps, precision, world=1):
     return {"workload": WORKLOAD, "model": "long-range Ising, J(r)=sum_k a_k b_k^r ~ 1/r^2, g=0.7",
             "L": cfg["L"], "D": cfg["D"], "N": cfg["N"], "w": 93, "tau": "-0.2i", "sweeps": sweeps,
@@ -276,7 +297,7 @@ def our_arm(args):
     flops = step_flops(dims, wd[:-1], wd[1:], cfg["d"], sweeps)
     ctx.launch_count(reset=True)
     ctx.prof_enable(True)
-    for c in range(4):
+    for c in range(NPROF):
         ctx.prof_read(c)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
@@ -289,7 +310,7 @@ def our_arm(args):
     ctx.prof_enable(False)
     ms = e0.elapsed_time(e1)
     launches = ctx.launch_count()
-    prof = {c: ctx.prof_read(c) for c in range(4)}
+    prof = {c: ctx.prof_read(c) for c in range(NPROF)}
     value, ms_max = replica_throughput(ms, args.steps * sweeps, "cuda")
     # observables after warmup + steps time steps against the oracle's stored values
     obs_err = None
@@ -361,13 +382,27 @@ def our_arm(args):
                     "useful_tflops": kfl / (kms / 1e3) / 1e12 if kms > 0 else None,
                     "peak_source": f"{src} bf16 sustained" + (" x 0.5 (tf32)" if base in (1, 2) else "")}
 
-        g64, gtc = prof[tv._lib.PROF_GEMM64], prof[tv._lib.PROF_GEMMTC]
+        def oz_roof(kms, kn, kfl):
+            peak = peaks.get("bf16_tflops_sustained", 1700.0)
+            achieved = OZ_PAIRS * kfl / (kms / 1e3) / 1e12 if kms > 0 else None
+            return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak if achieved else None, "traffic": traffic_from_profiles("oz_gemm_kernel"),
+                    "kernel": "oz_gemm_kernel (Ozaki-scheme fp64 GEMM on bf16 tcgen05; executed flops = useful x "
+                              f"{OZ_PAIRS} digit-slice products)",
+                    "launches": kn, "avg_launch_ms": kms / kn if kn else None, "passes": OZ_PAIRS,
+                    "useful_tflops": kfl / (kms / 1e3) / 1e12 if kms > 0 else None,
+                    "peak_source": f"{src} bf16 sustained"}
+
+        g64, gtc, goz = prof[tv._lib.PROF_GEMM64], prof[tv._lib.PROF_GEMMTC], prof[tv._lib.PROF_GEMMOZ]
         roofs = {}
         if g64[0] > 0:
             roofs["fp64_gemm"] = fp64_roof(g64[0], g64[1], g64[2])
         if gtc[0] > 0:
             roofs["tc_gemm"] = tc_roof(gtc[0], gtc[1], gtc[2])
-        dominant = "fp64_gemm" if g64[0] >= gtc[0] else "tc_gemm"
+        if goz[0] > 0:
+            roofs["oz_gemm"] = oz_roof(goz[0], goz[1], goz[2])
+        times = {"fp64_gemm": g64[0], "tc_gemm": gtc[0], "oz_gemm": goz[0]}
+        dominant = max(roofs, key=lambda k: times[k])
         roof = dict(roofs[dominant])
         roof["dominant_by_time"] = True
         other = [k for k in roofs if k != dominant]
@@ -376,7 +411,7 @@ def our_arm(args):
             "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "c128" if prec == 0 else f"{args.precision} contractions + c128 QR/final sweep",
+            "dtype": dtype_of(args.precision),
             "data": "synthetic",
             "config": config_of(cfg, sweeps, args.precision, world),
             "tflops": flops * args.steps * world / (ms_max / 1e3) / 1e12,
@@ -392,7 +427,7 @@ def our_arm(args):
             "obs_error": obs_err,
             "fp64_form": fp64_form,
             "clocks": clocks.summary(),
-            "kernel_ms": {name: prof[c][0] for c, name in enumerate(["gemm64", "gemm_tc", "qr", "form_q"])},
+            "kernel_ms": {name: prof[c][0] for c, name in enumerate(PROF_NAMES)},
         }
         print(json.dumps(line), flush=True)
     if world > 1:

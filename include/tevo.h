@@ -53,6 +53,20 @@ extern "C" {
  * cores, no fp64 rebuild or fp64 sweep; the QR, the norm and the reductions stay
  * fp64. Not the paper's recipe: an extra form for accuracy/speed studies. */
 #define TEVO_TC_ONLY 0x100
+/* OR-ed into any form: the fp64 contractions (the final sweep and the rebuild
+ * of the right environments of the low-precision forms; every sweep of
+ * TEVO_FP64) are computed on the bf16 tensor cores by the Ozaki splitting
+ * scheme: each operand row is scaled by a power of two and cut into integer
+ * digit slices of 7 bits, digit products are exact and their sums are exact in
+ * the fp32 accumulator, and the pass results are scaled and summed in fp64.
+ * With G slices the dropped part is about (G + 2) 2^(-7 G) of
+ * max|row of A| max|row of B| K per entry (G = 7: 49 bits; a native fp64 GEMM
+ * has about K 2^-53 of sum |A||B|). Inputs, outputs, the QR, the norm and the
+ * reductions stay fp64. TEVO_OZAKI_SLICES(G) picks G in 1..8 (default 7).
+ * Not in the paper: a GB300-specific way to run the fp64 sweep, whose fp64
+ * pipe is about 1/1600 of its bf16 tensor rate. */
+#define TEVO_OZAKI 0x200
+#define TEVO_OZAKI_SLICES(g) (TEVO_OZAKI | ((g) << 12))
 
 /* variants of the MPO construction (Secs. 3-6 of the paper) */
 #define TEVO_MPO_PLAIN 0     /* Algorithm 1 only (Eq. W1 at N = 1, Eq. W2 at N = 2) */
@@ -150,8 +164,10 @@ int mps_destroy(tevo_mps psi);
  * TEVO_FP64 / TF32 / TF32X3 / BF16X3: for the low-precision forms the first
  * sweeps-1 sweeps use tensor-core contractions and the last sweep (preceded by
  * a rebuild of the right environments) is fp64 (with sweeps = 1 the step is all
- * fp64); OR-ing TEVO_TC_ONLY makes every sweep a tensor-core sweep. The QR, the
- * norm and every reduction are fp64 in all forms.
+ * fp64); OR-ing TEVO_TC_ONLY makes every sweep a tensor-core sweep, OR-ing
+ * TEVO_OZAKI computes the fp64 contractions with the tensor-core Ozaki scheme
+ * (TEVO_OZAKI with TEVO_TC_ONLY is TEVO_EINVAL). The QR, the norm and every
+ * reduction are fp64 in all forms.
  * Errors: TEVO_EINVAL, TEVO_ESHAPE, TEVO_ETAU, TEVO_ENOMEM, TEVO_ECUDA,
  * TEVO_ENONFINITE (norm of the fitted state is 0, NaN or Inf), TEVO_ETIMEOUT
  * (a bounded device wait gave up), TEVO_EUNSUPPORTED. The work is issued on
@@ -171,6 +187,7 @@ int evolve_step(tevo_mps psi, tevo_mpo W, double tau_re, double tau_im, int D, i
  * once every chain is in right-canonical form and the schedule is chosen, a
  * step is captured into a CUDA graph (one per psi/phi buffer parity) and later
  * steps replay it. Handles must not be used from other streams meanwhile.
+ * TEVO_OZAKI is not built for the batched form (TEVO_EUNSUPPORTED).
  * Errors: as evolve_step, for the first failing chain. Synchronises.
  */
 int evolve_step_batched(tevo_mps* psis, const tevo_mpo* Ws, int n, int sweeps, int precision);
@@ -196,9 +213,10 @@ int mps_overlap(tevo_mps a, tevo_mps b, double* log_abs, double* phase);
  * tevo_gemm -- the complex contraction primitive of the sweep on its own:
  * C[m][n] = sum_k A[m][k] B[n][k] for complex fp64 device arrays A [M][K],
  * B [N][K] (row-major, k contiguous) and C [M][N] (row-major), computed in the
- * given precision: TEVO_FP64 on the fp64 pipe, the others on the tensor cores
- * (operands rounded/split into the precision's planes, fp32 accumulation, fp64
- * result). Device pointers, aligned to 16 bytes; temporary device memory comes
+ * given precision: TEVO_FP64 on the fp64 pipe, TEVO_FP64 | TEVO_OZAKI (or
+ * TEVO_OZAKI_SLICES(G)) as exact digit-slice products on the tensor cores, the
+ * others on the tensor cores (operands rounded/split into the precision's
+ * planes, fp32 accumulation, fp64 result). Device pointers, aligned to 16 bytes; temporary device memory comes
  * from the context's allocator and is released before returning.
  * Errors: TEVO_EINVAL, TEVO_ENOMEM, TEVO_ECUDA, TEVO_ETIMEOUT. Synchronises.
  */
@@ -259,7 +277,9 @@ int tevo_launch_count(tevo_ctx ctx, long long* count, int reset);
 #define TEVO_PROF_GEMMTC 1   /* tensor-core complex GEMM */
 #define TEVO_PROF_QR 2       /* Householder factorisation of one matrix (all its column steps) */
 #define TEVO_PROF_FORMQ 3    /* explicit thin Q */
-#define TEVO_PROF_CLASSES 4
+#define TEVO_PROF_GEMMOZ 4   /* Ozaki-scheme complex GEMM (slice products + split-K sum) */
+#define TEVO_PROF_OZSPLIT 5  /* row exponents and digit slices of the two Ozaki operands */
+#define TEVO_PROF_CLASSES 6
 int tevo_prof_enable(tevo_ctx ctx, int enable);
 int tevo_prof_read(tevo_ctx ctx, int cls, double* ms_total, long long* launches, double* flops_total,
                    double* bytes_total);

@@ -20,12 +20,12 @@ import os
 import numpy as np
 
 from . import _lib
-from ._lib import (FP64, TF32, TF32X3, BF16X3, TC_ONLY, MPO_PLAIN, MPO_EXACT, MPO_EXTENDED, MPO_FULL,  # noqa: F401
-                   TevoError)
+from ._lib import (FP64, TF32, TF32X3, BF16X3, TC_ONLY, OZAKI, OZAKI_SLICES, MPO_PLAIN, MPO_EXACT,  # noqa: F401
+                   MPO_EXTENDED, MPO_FULL, TevoError)
 
 __all__ = [
     "Context", "MPO", "MPS", "mpo_build", "mpo_build_host", "mps_init", "evolve_step", "evolve_step_batched", "measure_local", "mps_overlap",
-    "FP64", "TF32", "TF32X3", "BF16X3", "TC_ONLY", "MPO_PLAIN", "MPO_EXACT", "MPO_EXTENDED", "MPO_FULL",
+    "FP64", "TF32", "TF32X3", "BF16X3", "TC_ONLY", "OZAKI", "OZAKI_SLICES", "MPO_PLAIN", "MPO_EXACT", "MPO_EXTENDED", "MPO_FULL",
     "TevoError", "library_path",
 ]
 

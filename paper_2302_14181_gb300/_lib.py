@@ -17,8 +17,16 @@ lib = ctypes.CDLL(LIB_PATH)
 
 FP64, TF32, TF32X3, BF16X3 = 0, 1, 2, 3
 TC_ONLY = 0x100
+OZAKI = 0x200
+
+
+def OZAKI_SLICES(g):
+    """TEVO_OZAKI_SLICES(g): the Ozaki-scheme fp64 contractions with g digit slices."""
+    return OZAKI | (int(g) << 12)
+
+
 MPO_PLAIN, MPO_EXACT, MPO_EXTENDED, MPO_FULL = 0, 1, 2, 3
-PROF_GEMM64, PROF_GEMMTC, PROF_QR, PROF_FORMQ = 0, 1, 2, 3
+PROF_GEMM64, PROF_GEMMTC, PROF_QR, PROF_FORMQ, PROF_GEMMOZ, PROF_OZSPLIT = 0, 1, 2, 3, 4, 5
 
 
 class tevo_ctx(ctypes.c_void_p):

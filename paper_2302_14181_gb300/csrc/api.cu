@@ -125,6 +125,8 @@ struct tevo_mps_s {
   Buf qrflags;        // [0] error flag of the cooperative QR, [1..] reflector flags
   int qr_epoch = 0;
   bool coop_qr = true;  // off while a batched step issues (concurrent streams, graph capture)
+  int oz_slices = 0;    // > 0 while a step runs its fp64 contractions as Ozaki-scheme GEMMs
+  Buf oz_ws;            // digit slices, row exponents and split partials of those GEMMs
   int wmax = 0;
   MixedState* mixed = nullptr;
 };
@@ -133,8 +135,20 @@ namespace {
 
 double* scal(tevo_mps s, int k) { return reinterpret_cast<double*>(s->scalars.p) + k; }
 
+// slot of the scalars buffer holding the device error flag of the Ozaki GEMMs
+constexpr int OZ_FLAG_SLOT = 5;
+
 int gemm(tevo_mps s, const GemmDesc& g) {
   Launch L = launch_of(s->ctx);
+  if (s->oz_slices > 0) {
+    const size_t need = ozgemm64_workspace(g, s->oz_slices, L.num_sms);
+    if (need > 0) {
+      TRY(ensure(s->ctx, s->oz_ws, need));
+      const int e = ozgemm64(L, g, s->oz_slices, s->oz_ws.p, s->oz_ws.bytes,
+                             reinterpret_cast<int*>(scal(s, OZ_FLAG_SLOT)));
+      if (e != TEVO_EUNSUPPORTED) return e;
+    }
+  }
   return zgemm64(L, g, s->gemm_ws.p, s->gemm_ws.bytes);
 }
 
@@ -734,7 +748,7 @@ extern "C" int mps_destroy(tevo_mps s) {
   for (auto& b : s->A) dfree(c, b);
   for (auto& b : s->Anew) dfree(c, b);
   for (Buf* b : {&s->scalars, &s->env, &s->X, &s->T, &s->Bq, &s->V, &s->tau, &s->beta, &s->Atmp, &s->Rm,
-                 &s->gemm_ws, &s->red, &s->qrflags})
+                 &s->gemm_ws, &s->red, &s->qrflags, &s->oz_ws})
     dfree(c, *b);
   mixed_state_destroy(c, s->mixed);
   delete s;
@@ -746,9 +760,24 @@ extern "C" int mps_destroy(tevo_mps s) {
 // ---------------------------------------------------------------------------
 namespace {
 
+// slice count of an Ozaki precision flag (0 when the flag is absent, -1 when invalid)
+int oz_slices_of(int precision) {
+  if (!(precision & TEVO_OZAKI)) return (precision >> 12) ? -1 : 0;
+  const int g = (precision >> 12) & 0xF;
+  if (precision >> 16) return -1;
+  if (g == 0) return 7;
+  return g <= oz_max_slices() ? g : -1;
+}
+
+int strip_oz(int precision) { return precision & ~(TEVO_OZAKI | (0xF << 12)); }
+
 int check_step_args(tevo_mps s, tevo_mpo W, int sweeps, int precision) {
   if (!s || !W || sweeps < 1) return TEVO_EINVAL;
+  const int oz = oz_slices_of(precision);
+  if (oz < 0) return TEVO_EINVAL;
+  precision = strip_oz(precision);
   const bool tc_only = (precision & TEVO_TC_ONLY) != 0;
+  if (tc_only && oz) return TEVO_EINVAL;
   precision &= ~TEVO_TC_ONLY;
   if (precision < TEVO_FP64 || precision > TEVO_BF16X3) return TEVO_EINVAL;
   if (tc_only && precision == TEVO_FP64) return TEVO_EINVAL;
@@ -758,7 +787,21 @@ int check_step_args(tevo_mps s, tevo_mpo W, int sweeps, int precision) {
 
 // issue one time step on the context stream; no host synchronisation (so it can
 // be captured in a CUDA graph once the workspaces exist)
+int evolve_issue_body(tevo_mps s, tevo_mpo W, int sweeps, int precision, bool* mixed_out);
+
 int evolve_issue(tevo_mps s, tevo_mpo W, int sweeps, int precision, bool* mixed_out) {
+  const int oz = oz_slices_of(precision);
+  if (oz < 0) return TEVO_EINVAL;
+  if (oz && cudaMemsetAsync(scal(s, OZ_FLAG_SLOT), 0, sizeof(double), s->ctx->stream) != cudaSuccess)
+    return TEVO_ECUDA;
+  // the fp64 contractions of this step only (measure_local / mps_overlap stay native)
+  s->oz_slices = oz;
+  const int e = evolve_issue_body(s, W, sweeps, strip_oz(precision), mixed_out);
+  s->oz_slices = 0;
+  return e;
+}
+
+int evolve_issue_body(tevo_mps s, tevo_mpo W, int sweeps, int precision, bool* mixed_out) {
   const bool tc_only = (precision & TEVO_TC_ONLY) != 0;
   precision &= ~TEVO_TC_ONLY;
   tevo_ctx c = s->ctx;
@@ -805,13 +848,14 @@ int evolve_issue(tevo_mps s, tevo_mpo W, int sweeps, int precision, bool* mixed_
 // device flags of the step just issued (synchronises the context stream)
 int evolve_check(tevo_mps s, bool mixed) {
   tevo_ctx c = s->ctx;
-  int flag = 0, tflag = 0, qflag = 0;
+  int flag = 0, tflag = 0, qflag = 0, oflag = 0;
   TRYCUDA(cudaMemcpyAsync(&flag, scal(s, 4), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  TRYCUDA(cudaMemcpyAsync(&oflag, scal(s, OZ_FLAG_SLOT), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   if (s->qrflags.p)
     TRYCUDA(cudaMemcpyAsync(&qflag, s->qrflags.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   if (mixed) TRY(mixed_error_flag(c, s, &tflag));
   TRYCUDA(cudaStreamSynchronize(c->stream));
-  if (tflag || qflag) return TEVO_ETIMEOUT;
+  if (tflag || qflag || oflag) return TEVO_ETIMEOUT;
   if (flag) return TEVO_ENONFINITE;
   return 0;
 }
@@ -928,6 +972,7 @@ int batch_check(BatchPlan* p) {
 extern "C" int evolve_step_batched(tevo_mps* psis, const tevo_mpo* Ws, int n, int sweeps, int precision) {
   if (!psis || !Ws || n < 1) return TEVO_EINVAL;
   for (int c = 0; c < n; ++c) TRY(check_step_args(psis[c], Ws[c], sweeps, precision));
+  if (oz_slices_of(precision) != 0) return TEVO_EUNSUPPORTED;  // the Ozaki form is single-chain only
   for (int c = 0; c < n; ++c)
     for (int k = c + 1; k < n; ++k)
       if (psis[c] == psis[k]) return TEVO_EINVAL;
@@ -1159,12 +1204,29 @@ extern "C" int measure_local(tevo_mps s, int nops, const double* ops, double* ou
 extern "C" int tevo_gemm(tevo_ctx c, int precision, int M, int N, int K, const double* A, const double* B,
                          double* C) {
   if (!c || !A || !B || !C || M < 1 || N < 1 || K < 1) return TEVO_EINVAL;
+  const int oz = oz_slices_of(precision);
+  if (oz < 0 || (oz && strip_oz(precision) != TEVO_FP64)) return TEVO_EINVAL;
+  precision = strip_oz(precision);
   if (precision < TEVO_FP64 || precision > TEVO_BF16X3) return TEVO_EINVAL;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15)
     return TEVO_EINVAL;
   if (precision != TEVO_FP64) return mixed_gemm(c, precision, M, N, K, A, B, C);
   Buf ws;
   GemmDesc g = gd(A, 0, K, 1, B, 0, 1, K, C, 0, N, 1, M, N, K, 1);
+  if (oz) {
+    // [error flag | slices, exponents, partials]
+    int e = dalloc(c, ws, 256 + ozgemm64_workspace(g, oz, c->num_sms));
+    int flag = 0;
+    if (!e && cudaMemsetAsync(ws.p, 0, sizeof(int), c->stream) != cudaSuccess) e = TEVO_ECUDA;
+    if (!e)
+      e = ozgemm64(launch_of(c), g, oz, static_cast<char*>(ws.p) + 256, ws.bytes - 256, static_cast<int*>(ws.p));
+    if (!e && (cudaMemcpyAsync(&flag, ws.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+               cudaStreamSynchronize(c->stream) != cudaSuccess))
+      e = TEVO_ECUDA;
+    dfree(c, ws);
+    if (!e && flag) e = TEVO_ETIMEOUT;
+    return e;
+  }
   size_t need = zgemm64_workspace(g, c->num_sms);
   int e = dalloc(c, ws, need);
   if (!e) e = zgemm64(launch_of(c), g, ws.p, ws.bytes);

@@ -1,0 +1,502 @@
+// Complex fp64 GEMM emulated on the bf16 tensor cores: the splitting form of the
+// Ozaki scheme (error-free products of integer digit slices).
+//
+//   C[m][n] = sum_k A[m][k] * B[n][k]      (fp64 complex in, fp64 complex out)
+//
+// Every row r of an operand is scaled by a power of two 2^-e_r with
+// max_k max(|Re|, |Im|) < 2^e_r, and the scaled row (entries in (-1, 1)) is cut
+// into G digit slices
+//   x = 2^e_r * sum_s alpha_s * 2^-(P + W s) + rest,   |alpha_s| <= 2^P,
+// taken greedily with round-to-nearest (alpha_s = rint of the remaining part in
+// units of 2^-(P + W s)), P = 6, W = 7 bits per slice, |rest| <= 2^(e_r - W G).
+// The digits are integers of at most 7 significant bits, so they are exact in
+// bf16, their products (at most 2^12) are exact, and a sum of up to 4096 such
+// products is an integer below 2^24: exact in the fp32 accumulator of the
+// tensor core, whatever the order of summation.
+//
+// C is formed from the slice pairs (s, t) with s + t < G, grouped by g = s + t
+// (all pairs of a group carry the weight 2^-(2P + W g)). One pass accumulates a
+// group over a chunk of at most 256 K-indices: 2 (g + 1) * 256 <= 4096 terms, so
+// the pass result is exact. The epilogue multiplies it by
+// 2^(e_m + e_n - 2P - W g) (exact) and adds it to the fp64 output tile. The only
+// rounding errors are those fp64 additions and the dropped terms (digits past
+// slice G-1 and pairs with s + t >= G), relative size about (G + 2) 2^-(W G) of
+// max|A_m.| max|B_n.| K: G = 7 gives 49 bits.
+//
+// The tensor-core schedule is that of the plain complex GEMM (k_tc.cu): a
+// persistent CTA per SM, a TMA producer warp, one thread issuing tcgen05.mma,
+// four epilogue warps, two tensor-memory accumulator buffers (a pass drains
+// while the next accumulates). A stage holds the (re, im) planes of one A slice
+// and of one B slice for 32 K-indices; it feeds four real MMAs per 16 K:
+//   Re += Ar Br - Ai Bi,   Im += Ar Bi + Ai Br.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+
+#include "tc_ptx.cuh"
+#include "tevo_internal.h"
+#include "tevo_tc.h"
+
+namespace tevo {
+
+namespace {
+
+constexpr int OZ_P = 6;           // digits are integers in [-2^P, 2^P]
+constexpr int OZ_W = 7;           // weight ratio between consecutive slices: 2^W
+constexpr int OZ_MAX_SLICES = 8;  // (g + 1) * 256 <= 2048 keeps every pass below 2^24
+constexpr int OZ_TM = 128, OZ_TN = 128;
+constexpr int OZ_KCB = 64;                 // bytes of K per stage row (32 bf16)
+constexpr int OZ_KT_CHUNK = 8;             // K-tiles of 32 per exact chunk: 256 K-indices
+constexpr int OZ_NSTAGE = 6;
+constexpr int OZ_A_BYTES = 2 * OZ_TM * OZ_KCB;  // re, im planes of one slice: 16 KB
+constexpr int OZ_B_BYTES = 2 * OZ_TN * OZ_KCB;
+constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
+constexpr int OZ_SMEM_BYTES = OZ_NSTAGE * OZ_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int OZ_THREADS = 192;
+
+// one operand to cut into digit slices: element (r, k) of R x K at
+// src[r * sR + k * sK] (conjugated when conj), digit planes written to
+// dst[p * plane_stride + r * row_pitch + k], row exponents to exps[r]
+struct OzSplit {
+  const double2* src;
+  long long sR, sK;
+  int R, K;
+  int conj;
+  int G;
+  __nv_bfloat16* dst;
+  long long plane_stride, row_pitch;
+  int* exps;
+};
+
+struct OzArgs {
+  int M, N, G;
+  int k_tiles, nchunks, cps, splits;  // K-tiles of 32, exact chunks, chunks per split
+  const int* ea;                      // row exponents of A (M) and of B (N)
+  const int* eb;
+  double2* C;  // output when splits == 1
+  long long sCm, sCn;
+  double2* part;  // [splits][M][N] when splits > 1
+  int* err;
+};
+
+// exponent e with |x| < 2^e for the largest entry of a row (0 for a zero row)
+__device__ __forceinline__ int row_exponent(double mx) {
+  if (!(mx > 0.0)) return 0;
+  int e;
+  frexp(mx, &e);
+  return e;
+}
+
+// one warp per row (K contiguous or both strides general)
+__global__ void oz_rowexp_warp_kernel(OzSplit o) {
+  const int warps = blockDim.x / 32;
+  const int lane = threadIdx.x % 32;
+  for (long long r = (long long)blockIdx.x * warps + threadIdx.x / 32; r < o.R; r += (long long)gridDim.x * warps) {
+    double mx = 0.0;
+    for (int k = lane; k < o.K; k += 32) {
+      const double2 v = o.src[r * o.sR + (long long)k * o.sK];
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) o.exps[r] = row_exponent(mx);
+  }
+}
+
+// one thread per row (rows contiguous: consecutive lanes read consecutive rows)
+__global__ void oz_rowexp_lane_kernel(OzSplit o) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < o.R; r += (long long)gridDim.x * blockDim.x) {
+    double mx = 0.0;
+    for (int k = 0; k < o.K; ++k) {
+      const double2 v = o.src[r * o.sR + (long long)k * o.sK];
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+    o.exps[r] = row_exponent(mx);
+  }
+}
+
+// digit planes [2G][R][row_pitch] (plane 2s = Re of slice s, 2s+1 = Im) of a
+// 32 x 32 tile, staged in shared memory so that both the fp64 reads (along the
+// contiguous source index) and the bf16 writes (along K) are coalesced
+template <bool ROWS_CONTIG>
+__global__ void oz_slice_kernel(OzSplit o) {
+  __shared__ double2 tile[32][33];
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int rr = ROWS_CONTIG ? threadIdx.x : i, kk = ROWS_CONTIG ? i : threadIdx.x;
+    const int r = r0 + rr, k = k0 + kk;
+    double2 v = make_double2(0.0, 0.0);
+    if (r < o.R && k < o.K) v = o.src[(long long)r * o.sR + (long long)k * o.sK];
+    if (o.conj) v.y = -v.y;
+    tile[rr][kk] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, k = k0 + threadIdx.x;
+    if (r >= o.R || k >= o.K) continue;
+    const double2 v = tile[i][threadIdx.x];
+    const int e = o.exps[r];
+    double xr = ldexp(v.x, -e), xi = ldexp(v.y, -e);  // in (-1, 1)
+    __nv_bfloat16* dst = o.dst + (long long)r * o.row_pitch + k;
+    double up = (double)(1 << OZ_P);  // 2^(P + W s)
+    for (int s = 0; s < o.G; ++s) {
+      const double dr = rint(xr * up), di = rint(xi * up);
+      xr -= dr / up;  // exact: the digit is the nearest multiple of 2^-(P + W s)
+      xi -= di / up;
+      dst[(long long)(2 * s) * o.plane_stride] = __float2bfloat16_rn((float)dr);
+      dst[(long long)(2 * s + 1) * o.plane_stride] = __float2bfloat16_rn((float)di);
+      up *= (double)(1 << OZ_W);
+    }
+  }
+}
+
+// fixed-order sum of the fp64 split partials into the strided output
+__global__ void oz_reduce_kernel(const double2* P, int splits, int M, int N, double2* C, long long sCm,
+                                 long long sCn) {
+  const long long total = (long long)M * N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int m = int(idx / N), n = int(idx % N);
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < splits; ++s) {
+      const double2 v = P[((long long)s * M + m) * N + n];
+      re += v.x;
+      im += v.y;
+    }
+    C[m * sCm + n * sCn] = make_double2(re, im);
+  }
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_NSTAGE * OZ_STAGE_BYTES);
+  // barriers: full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2]; then the TMEM address slot
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_NSTAGE + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + OZ_NSTAGE);
+  const uint32_t tfull0 = smem_u32(bars + 2 * OZ_NSTAGE), tempty0 = smem_u32(bars + 2 * OZ_NSTAGE + 2);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  const int mt = (a.M + OZ_TM - 1) / OZ_TM, nt = (a.N + OZ_TN - 1) / OZ_TN;
+  const int nunits = mt * nt * a.splits;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_NSTAGE; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 4);  // one arrival per epilogue warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  // unit u -> (split z, row tile, column tile) and its chunk range [c0, c1)
+  auto unit_of = [&](int u, int& m0, int& n0, int& c0, int& c1) {
+    const int z = u / (mt * nt), r = u % (mt * nt);
+    m0 = (r / nt) * OZ_TM;
+    n0 = (r % nt) * OZ_TN;
+    c0 = z * a.cps;
+    c1 = min(a.nchunks, c0 + a.cps);
+    return z;
+  };
+  auto chunk_tiles = [&](int c, int& kt0, int& kt1) {
+    kt0 = c * OZ_KT_CHUNK;
+    kt1 = min(a.k_tiles, kt0 + OZ_KT_CHUNK);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      long long q = 0;  // stage ring counter
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        int m0, n0, c0, c1;
+        unit_of(u, m0, n0, c0, c1);
+        for (int c = c0; c < c1 && ok; ++c) {
+          int kt0, kt1;
+          chunk_tiles(c, kt0, kt1);
+          for (int g = 0; g < a.G && ok; ++g)
+            for (int kt = kt0; kt < kt1 && ok; ++kt)
+              for (int s = 0; s <= g; ++s, ++q) {
+                const int st = int(q % OZ_NSTAGE);
+                if (!mbar_wait(empty0 + 8 * st, (uint32_t(q / OZ_NSTAGE) & 1u) ^ 1u, a.err, 1)) {
+                  ok = false;
+                  break;
+                }
+                const uint32_t fb = full0 + 8 * st;
+                mbar_expect_tx(fb, OZ_STAGE_BYTES);
+                uint8_t* sp = smem + st * OZ_STAGE_BYTES;
+                tma_load_4d(smem_u32(sp), &tmA, kt * 32, 0, m0, 2 * s, fb);
+                tma_load_4d(smem_u32(sp + OZ_A_BYTES), &tmB, kt * 32, 0, n0, 2 * (g - s), fb);
+              }
+        }
+      }
+      // do not leave while copies are in flight
+      for (long long r = (q > OZ_NSTAGE ? q - OZ_NSTAGE : 0); r < q; ++r)
+        mbar_wait(full0 + 8 * int(r % OZ_NSTAGE), uint32_t(r / OZ_NSTAGE) & 1u, a.err, 2);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // instruction descriptor: fp32 accumulate, bf16 A and B, K-major, M = 128, N = 128
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) |
+                             ((uint32_t)(OZ_TM >> 4) << 24);
+      const uint32_t neg = 1u << 13;  // negate A
+      const uint64_t plane_a = (uint64_t)((OZ_TM * OZ_KCB) >> 4), plane_b = (uint64_t)((OZ_TN * OZ_KCB) >> 4);
+      long long q = 0;
+      int i = 0;  // pass counter
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        int m0, n0, c0, c1;
+        unit_of(u, m0, n0, c0, c1);
+        for (int c = c0; c < c1 && ok; ++c) {
+          int kt0, kt1;
+          chunk_tiles(c, kt0, kt1);
+          for (int g = 0; g < a.G && ok; ++g, ++i) {
+            const int b = i & 1;
+            if (!mbar_wait(tempty0 + 8 * b, (uint32_t(i >> 1) & 1u) ^ 1u, a.err, 5)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dre = tmem + (uint32_t)(b * 2 * OZ_TN), dim = dre + OZ_TN;
+            bool first = true;
+            for (int kt = kt0; kt < kt1 && ok; ++kt)
+              for (int s = 0; s <= g; ++s, ++q) {
+                const int st = int(q % OZ_NSTAGE);
+                if (!mbar_wait(full0 + 8 * st, uint32_t(q / OZ_NSTAGE) & 1u, a.err, 3)) {
+                  ok = false;
+                  break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = smem_u32(smem + st * OZ_STAGE_BYTES);
+                const uint64_t ar = sdesc(sa), br = sdesc(sa + OZ_A_BYTES);
+#pragma unroll
+                for (int ks = 0; ks < OZ_KCB / 32; ++ks) {
+                  const uint64_t o = (uint64_t)((ks * 32) >> 4);
+                  const uint32_t acc = first ? 0u : 1u;
+                  mma<TC_BF16>(dre, ar + o, br + o, idesc, acc);                       // Re  = Ar Br
+                  mma<TC_BF16>(dre, ar + plane_a + o, br + plane_b + o, idesc | neg, 1u);  // Re -= Ai Bi
+                  mma<TC_BF16>(dim, ar + o, br + plane_b + o, idesc, acc);             // Im  = Ar Bi
+                  mma<TC_BF16>(dim, ar + plane_a + o, br + o, idesc, 1u);              // Im += Ai Br
+                  first = false;
+                }
+                mma_commit(empty0 + 8 * st);
+              }
+            mma_commit(tfull0 + 8 * b);
+          }
+        }
+      }
+    }
+  } else {
+    // epilogue: warps 2..5 own tensor-memory lane quarters (warp % 4)
+    const int qw = warp % 4;
+    int i = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+      int m0, n0, c0, c1;
+      const int z = unit_of(u, m0, n0, c0, c1);
+      const int m = m0 + qw * 32 + lane;
+      const int em = m < a.M ? a.ea[m] : 0;
+      for (int c = c0; c < c1 && ok; ++c)
+        for (int g = 0; g < a.G; ++g, ++i) {
+          const int b = i & 1;
+          if (!mbar_wait(tfull0 + 8 * b, uint32_t(i >> 1) & 1u, a.err, 4)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const bool overwrite = (c == c0 && g == 0);
+          const int sh = em - 2 * OZ_P - OZ_W * g;
+          const uint32_t trow = tmem + (uint32_t)(b * 2 * OZ_TN) + ((uint32_t)(qw * 32) << 16);
+          for (int cc = 0; cc < OZ_TN; cc += 32) {
+            uint32_t rr[32], ri[32];
+            tmem_ld32(trow + cc, rr);
+            tmem_ld32(trow + OZ_TN + cc, ri);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (m >= a.M) continue;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int n = n0 + cc + j;
+              if (n >= a.N) continue;
+              const int e = sh + a.eb[n];
+              const double vr = ldexp((double)__uint_as_float(rr[j]), e);
+              const double vi = ldexp((double)__uint_as_float(ri[j]), e);
+              double2* dst = a.splits == 1 ? a.C + (long long)m * a.sCm + (long long)n * a.sCn
+                                           : a.part + ((long long)z * a.M + m) * (long long)a.N + n;
+              if (overwrite) {
+                *dst = make_double2(vr, vi);
+              } else {
+                const double2 old = *dst;
+                *dst = make_double2(old.x + vr, old.y + vi);
+              }
+            }
+          }
+          // this warp is done reading the buffer: hand it back to the MMA warp
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+        }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+inline size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+inline long long pad8(long long x) { return (x + 7) / 8 * 8; }
+
+int grid_of(long long n, int per_block, int sms) {
+  long long b = (n + per_block - 1) / per_block;
+  if (b > 16LL * sms) b = 16LL * sms;
+  return int(b < 1 ? 1 : b);
+}
+
+struct OzPlan {
+  int k_tiles, nchunks, cps, splits;
+  size_t a_bytes, b_bytes, e_bytes, p_bytes;
+};
+
+OzPlan plan(int M, int N, int K, int G, int num_sms) {
+  OzPlan p{};
+  p.k_tiles = (K + 31) / 32;
+  p.nchunks = (p.k_tiles + OZ_KT_CHUNK - 1) / OZ_KT_CHUNK;
+  const long long tiles = (long long)((M + OZ_TM - 1) / OZ_TM) * ((N + OZ_TN - 1) / OZ_TN);
+  int splits = (int)std::max<long long>(1, std::min<long long>((num_sms + tiles - 1) / tiles, p.nchunks));
+  splits = std::min(splits, 64);
+  p.cps = (p.nchunks + splits - 1) / splits;
+  p.splits = (p.nchunks + p.cps - 1) / p.cps;
+  const long long kp = pad8(K);
+  p.a_bytes = al256((size_t)2 * G * M * kp * 2);
+  p.b_bytes = al256((size_t)2 * G * N * kp * 2);
+  p.e_bytes = al256((size_t)(M + N) * sizeof(int));
+  p.p_bytes = p.splits > 1 ? al256((size_t)p.splits * M * N * 16) : 0;
+  return p;
+}
+
+int split_operand(const Launch& L, const OzSplit& o) {
+  const bool rows_contig = o.sR == 1 && o.sK != 1;
+  if (rows_contig)
+    oz_rowexp_lane_kernel<<<grid_of(o.R, 256, L.num_sms), 256, 0, L.stream>>>(o);
+  else
+    oz_rowexp_warp_kernel<<<grid_of((long long)o.R * 32, 256, L.num_sms), 256, 0, L.stream>>>(o);
+  ++*L.launches;
+  if ((o.R + 31) / 32 > 65535) return TEVO_ESHAPE;
+  dim3 grid((o.K + 31) / 32, (o.R + 31) / 32), block(32, 8);
+  if (rows_contig)
+    oz_slice_kernel<true><<<grid, block, 0, L.stream>>>(o);
+  else
+    oz_slice_kernel<false><<<grid, block, 0, L.stream>>>(o);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+}  // namespace
+
+int oz_max_slices() { return OZ_MAX_SLICES; }
+
+size_t ozgemm64_workspace(const GemmDesc& g, int slices, int num_sms) {
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0 || slices < 1 || slices > OZ_MAX_SLICES) return 0;
+  const OzPlan p = plan(g.M, g.N, g.K, slices, num_sms);
+  return p.a_bytes + p.b_bytes + p.e_bytes + p.p_bytes;
+}
+
+int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws_bytes, int* err) {
+  if (g.batch != 1 || g.conjB || g.alpha_re != 1.0 || g.alpha_im != 0.0 || g.beta_re != 0.0 || g.beta_im != 0.0)
+    return TEVO_EUNSUPPORTED;
+  if (slices < 1 || slices > OZ_MAX_SLICES) return TEVO_EINVAL;
+  if (g.M <= 0 || g.N <= 0) return 0;
+  if (g.K <= 0) return TEVO_EUNSUPPORTED;
+  static bool attr_done = false;
+  if (!attr_done) {
+    if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES) !=
+        cudaSuccess)
+      return TEVO_ECUDA;
+    attr_done = true;
+  }
+  const OzPlan p = plan(g.M, g.N, g.K, slices, L.num_sms);
+  if (!ws || !err || ws_bytes < p.a_bytes + p.b_bytes + p.e_bytes + p.p_bytes) return TEVO_ESHAPE;
+  char* w = static_cast<char*>(ws);
+  __nv_bfloat16* da = reinterpret_cast<__nv_bfloat16*>(w);
+  w += p.a_bytes;
+  __nv_bfloat16* db = reinterpret_cast<__nv_bfloat16*>(w);
+  w += p.b_bytes;
+  int* ea = reinterpret_cast<int*>(w);
+  int* eb = ea + g.M;
+  w += p.e_bytes;
+  double2* part = p.splits > 1 ? reinterpret_cast<double2*>(w) : nullptr;
+  const long long kp = pad8(g.K);
+  // A(m, k) at A + m sAm + k sAk; B(k, n) at B + k sBk + n sBn, read as rows n
+  OzSplit sa{static_cast<const double2*>(g.A), g.sAm, g.sAk, g.M, g.K, g.conjA, slices, da, (long long)g.M * kp, kp,
+             ea};
+  OzSplit sb{static_cast<const double2*>(g.B), g.sBn, g.sBk, g.N, g.K, 0, slices, db, (long long)g.N * kp, kp, eb};
+  const int pr_split = L.prof ? L.prof->begin(L.stream, TEVO_PROF_OZSPLIT, 0.0,
+                                              (16.0 + 4.0 * slices) * ((double)g.M + g.N) * g.K)
+                              : -1;
+  int e = split_operand(L, sa);
+  if (!e) e = split_operand(L, sb);
+  if (L.prof) L.prof->end(L.stream, pr_split);
+  if (e) return e;
+
+  TcOperand oa{da, 2, 2 * slices, (long long)g.M * kp, g.M, kp, g.K, 1, kp};
+  TcOperand ob{db, 2, 2 * slices, (long long)g.N * kp, g.N, kp, g.K, 1, kp};
+  CUtensorMap ma, mb;
+  e = tc_make_map(&ma, oa, OZ_TM, 2);
+  if (!e) e = tc_make_map(&mb, ob, OZ_TN, 2);
+  if (e) return e;
+  OzArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.M = g.M;
+  a.N = g.N;
+  a.G = slices;
+  a.k_tiles = p.k_tiles;
+  a.nchunks = p.nchunks;
+  a.cps = p.cps;
+  a.splits = p.splits;
+  a.ea = ea;
+  a.eb = eb;
+  a.C = static_cast<double2*>(g.C);
+  a.sCm = g.sCm;
+  a.sCn = g.sCn;
+  a.part = part;
+  a.err = err;
+  const long long units = (long long)((g.M + OZ_TM - 1) / OZ_TM) * ((g.N + OZ_TN - 1) / OZ_TN) * p.splits;
+  if (units > (1LL << 30)) return TEVO_ESHAPE;
+  dim3 grid((unsigned)std::min<long long>(units, (long long)L.num_sms));
+  const double useful = 8.0 * (double)g.M * g.N * g.K;
+  const int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_GEMMOZ, useful, 16.0 * ((double)g.M * g.K + (double)g.N * g.K +
+                                                                                   (double)g.M * g.N))
+                        : -1;
+  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, L.stream>>>(ma, mb, a);
+  ++*L.launches;
+  if (p.splits > 1) {
+    oz_reduce_kernel<<<grid_of((long long)g.M * g.N, 256, L.num_sms), 256, 0, L.stream>>>(
+        part, p.splits, g.M, g.N, static_cast<double2*>(g.C), g.sCm, g.sCn);
+    ++*L.launches;
+  }
+  if (L.prof) L.prof->end(L.stream, pr);
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+}  // namespace tevo

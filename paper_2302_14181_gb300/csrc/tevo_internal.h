@@ -77,6 +77,14 @@ struct Launch {
 size_t zgemm64_workspace(const GemmDesc& g, int num_sms);
 int zgemm64(const Launch& L, const GemmDesc& g, void* workspace, size_t ws_bytes);
 
+// fp64 complex GEMM on the bf16 tensor cores by the Ozaki splitting scheme
+// (k_oz.cu): batch 1, alpha 1, beta 0, conjB 0 only (else TEVO_EUNSUPPORTED);
+// slices in 1..oz_max_slices(). A device wait that gives up sets *err (never
+// cleared here).
+int oz_max_slices();
+size_t ozgemm64_workspace(const GemmDesc& g, int slices, int num_sms);
+int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws_bytes, int* err);
+
 // G2 over the nonzeros of the MPO operand (CSR rows of [(s v)][(wl s')]):
 // T[p][r][b] = sum_k W[r][k] X[p][k][b], batch p, R rows, K = wl d, Db columns
 int zsparse_g2(const Launch& L, const z64* X, z64* T, const int* row_ptr, const int* col_idx, const z64* vals,
