@@ -7,8 +7,11 @@
 // max_k max(|Re|, |Im|) < 2^e_r, and the scaled row (entries in (-1, 1)) is cut
 // into G digit slices
 //   x = 2^e_r * sum_s alpha_s * 2^-(P + W s) + rest,   |alpha_s| <= 2^P,
-// taken greedily with round-to-nearest (alpha_s = rint of the remaining part in
-// units of 2^-(P + W s)), P = 6, W = 7 bits per slice, |rest| <= 2^(e_r - W G).
+// taken greedily with round-to-nearest (alpha_s = the remaining part in units of
+// 2^-(P + W s), rounded to the nearest integer), P = 6, W = 7 bits per slice,
+// |rest| <= 2^(e_r - W G). Scaling and slicing work on the bit patterns with
+// integer operations (x 2^-e_r as a fixed-point integer of P + W (G - 1)
+// fraction bits); a row holding a NaN or an infinity gives NaN outputs.
 // The digits are integers of at most 7 significant bits, so they are exact in
 // bf16, their products (at most 2^12) are exact, and a sum of up to 4096 such
 // products is an integer below 2^24: exact in the fp32 accumulator of the
@@ -17,11 +20,14 @@
 // C is formed from the slice pairs (s, t) with s + t < G, grouped by g = s + t
 // (all pairs of a group carry the weight 2^-(2P + W g)). One pass accumulates a
 // group over a chunk of at most 256 K-indices: 2 (g + 1) * 256 <= 4096 terms, so
-// the pass result is exact. The epilogue multiplies it by
-// 2^(e_m + e_n - 2P - W g) (exact) and adds it to the fp64 output tile. The only
-// rounding errors are those fp64 additions and the dropped terms (digits past
-// slice G-1 and pairs with s + t >= G), relative size about (G + 2) 2^-(W G) of
-// max|A_m.| max|B_n.| K: G = 7 gives 49 bits.
+// the pass result is exact. The epilogue turns it into an integer and adds it,
+// shifted by its group's weight, to a 64-bit fixed-point sum per output entry;
+// after the last pass of a tile the sum is scaled by 2^(e_m + e_n) and rounded
+// once to fp64. The only errors are the dropped terms (digits past slice G-1
+// and pairs with s + t >= G), relative size about (G + 2) 2^-(W G) of
+// max|A_m.| max|B_n.| K (G = 7: 49 bits), the few bits of the last groups
+// below the fixed-point unit, and that final rounding. No per-pass work uses
+// the fp64 pipe, which on this part runs at about 1/1600 of the bf16 MMA rate.
 //
 // The tensor-core schedule is that of the plain complex GEMM (k_tc.cu): a
 // persistent CTA per SM, a TMA producer warp, one thread issuing tcgen05.mma,
@@ -34,6 +40,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 
@@ -80,15 +87,92 @@ struct OzArgs {
   double2* C;  // output when splits == 1
   long long sCm, sCn;
   double2* part;  // [splits][M][N] when splits > 1
+  longlong2* acc;  // fixed-point sums: [CTA][column][row] of one 128 x 128 tile per CTA
+  int base_shift;  // S unit: 2^-base_shift of a group-0 pass value
   int* err;
 };
 
-// exponent e with |x| < 2^e for the largest entry of a row (0 for a zero row)
-__device__ __forceinline__ int row_exponent(double mx) {
-  if (!(mx > 0.0)) return 0;
-  int e;
-  frexp(mx, &e);
-  return e;
+// row exponent marking a row that holds a NaN or an infinity: its digits are
+// zero and every output entry it touches is NaN
+constexpr int OZ_NONFINITE = 0x7fff0000;
+
+// exponent e with |x| < 2^e for the largest magnitude of a row, given the bit
+// pattern of that magnitude (0 for a zero row). Non-negative doubles order like
+// their bit patterns, so the row maximum is taken on integers.
+__device__ __forceinline__ int row_exponent_bits(unsigned long long mx) {
+  if (mx == 0) return 0;
+  const int E = (int)(mx >> 52);  // sign bit already cleared
+  if (E == 0x7FF) return OZ_NONFINITE;
+  return E == 0 ? -1022 : E - 1022;
+}
+
+__device__ __forceinline__ unsigned long long mag_bits(double2 v) {
+  const unsigned long long ax = (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long ay = (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull;
+  return ax > ay ? ax : ay;
+}
+
+// x * 2^(F - e) rounded to the nearest integer (ties to even), for |x| < 2^e:
+// the common fixed point of a row's digits (F = P + W (G - 1) <= 55 bits)
+__device__ __forceinline__ long long to_fixed(double x, int e, int F) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  unsigned long long m = b & ((1ull << 52) - 1ull);
+  if (E == 0 && m == 0) return 0;
+  if (E != 0) m |= 1ull << 52;
+  const int sh = (E == 0 ? 1 : E) - 1075 - e + F;  // x = m 2^(E - 1075)
+  unsigned long long X;
+  if (sh >= 0) {
+    X = m << sh;  // < 2^F since |x| < 2^e
+  } else if (sh <= -64) {
+    X = 0;
+  } else {
+    const int q = -sh;
+    X = m >> q;
+    const unsigned long long rem = m & ((1ull << q) - 1ull), half = 1ull << (q - 1);
+    if (rem > half || (rem == half && (X & 1ull))) ++X;
+  }
+  return (b >> 63) ? -(long long)X : (long long)X;
+}
+
+// s * 2^e2 in fp64, rounded to nearest (ties to even), assembled from the
+// binary64 fields with integer operations; results outside the normal range
+// take the conversion instruction and an exact power-of-two scaling instead
+__host__ __device__ inline double fixed_to_f64(long long s, int e2) {
+  if (s == 0) return 0.0;
+  const unsigned long long neg = (unsigned long long)s >> 63;
+  const unsigned long long u = neg ? 0ull - (unsigned long long)s : (unsigned long long)s;
+#ifdef __CUDA_ARCH__
+  const int nb = 64 - __clzll((long long)u);
+#else
+  const int nb = 64 - __builtin_clzll(u);
+#endif
+  const int ex = nb - 1 + e2;  // exponent of the leading bit
+  if (ex < -1022 || ex > 1022) return ldexp((double)s, e2);
+  unsigned long long q;
+  int exq = ex;
+  if (nb <= 53) {
+    q = u << (53 - nb);
+  } else {
+    const int drop = nb - 53;  // 1..11 bits below the 53 kept
+    q = u >> drop;
+    const unsigned long long rem = u & ((1ull << drop) - 1ull), half = 1ull << (drop - 1);
+    if (rem > half || (rem == half && (q & 1ull))) {
+      ++q;
+      if (q >> 53) {
+        q >>= 1;
+        ++exq;
+      }
+    }
+  }
+  const unsigned long long bits = (neg << 63) | ((unsigned long long)(exq + 1023) << 52) | (q & ((1ull << 52) - 1ull));
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)bits);
+#else
+  double d;
+  std::memcpy(&d, &bits, sizeof(d));
+  return d;
+#endif
 }
 
 // one warp per row (K contiguous or both strides general)
@@ -96,26 +180,29 @@ __global__ void oz_rowexp_warp_kernel(OzSplit o) {
   const int warps = blockDim.x / 32;
   const int lane = threadIdx.x % 32;
   for (long long r = (long long)blockIdx.x * warps + threadIdx.x / 32; r < o.R; r += (long long)gridDim.x * warps) {
-    double mx = 0.0;
+    unsigned long long mx = 0;
     for (int k = lane; k < o.K; k += 32) {
-      const double2 v = o.src[r * o.sR + (long long)k * o.sK];
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      const unsigned long long v = mag_bits(o.src[r * o.sR + (long long)k * o.sK]);
+      mx = v > mx ? v : mx;
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0) o.exps[r] = row_exponent(mx);
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, off);
+      mx = v > mx ? v : mx;
+    }
+    if (lane == 0) o.exps[r] = row_exponent_bits(mx);
   }
 }
 
 // one thread per row (rows contiguous: consecutive lanes read consecutive rows)
 __global__ void oz_rowexp_lane_kernel(OzSplit o) {
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < o.R; r += (long long)gridDim.x * blockDim.x) {
-    double mx = 0.0;
+    unsigned long long mx = 0;
     for (int k = 0; k < o.K; ++k) {
-      const double2 v = o.src[r * o.sR + (long long)k * o.sK];
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      const unsigned long long v = mag_bits(o.src[r * o.sR + (long long)k * o.sK]);
+      mx = v > mx ? v : mx;
     }
-    o.exps[r] = row_exponent(mx);
+    o.exps[r] = row_exponent_bits(mx);
   }
 }
 
@@ -140,16 +227,25 @@ __global__ void oz_slice_kernel(OzSplit o) {
     if (r >= o.R || k >= o.K) continue;
     const double2 v = tile[i][threadIdx.x];
     const int e = o.exps[r];
-    double xr = ldexp(v.x, -e), xi = ldexp(v.y, -e);  // in (-1, 1)
     __nv_bfloat16* dst = o.dst + (long long)r * o.row_pitch + k;
-    double up = (double)(1 << OZ_P);  // 2^(P + W s)
+    // greedy digits of the fixed-point value, most significant first: digit s
+    // is the nearest integer (ties to even) to the remainder in units of 2^q,
+    // q = W (G - 1 - s); integer arithmetic only
+    const int F = OZ_P + OZ_W * (o.G - 1);
+    long long xr = e == OZ_NONFINITE ? 0 : to_fixed(v.x, e, F);
+    long long xi = e == OZ_NONFINITE ? 0 : to_fixed(v.y, e, F);
     for (int s = 0; s < o.G; ++s) {
-      const double dr = rint(xr * up), di = rint(xi * up);
-      xr -= dr / up;  // exact: the digit is the nearest multiple of 2^-(P + W s)
-      xi -= di / up;
+      const int q = OZ_W * (o.G - 1 - s);
+      long long dr = xr, di = xi;
+      if (q > 0) {
+        const long long bias = (1LL << (q - 1)) - 1;
+        dr = (xr + bias + ((xr >> q) & 1)) >> q;
+        di = (xi + bias + ((xi >> q) & 1)) >> q;
+      }
+      xr -= dr * (1LL << q);
+      xi -= di * (1LL << q);
       dst[(long long)(2 * s) * o.plane_stride] = __float2bfloat16_rn((float)dr);
       dst[(long long)(2 * s + 1) * o.plane_stride] = __float2bfloat16_rn((float)di);
-      up *= (double)(1 << OZ_W);
     }
   }
 }
@@ -207,10 +303,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   // unit u -> (split z, row tile, column tile) and its chunk range [c0, c1)
+  // the shorter tile dimension runs fastest, so CTAs that run together share
+  // the tiles of the longer operand (read once from DRAM, then from L2)
   auto unit_of = [&](int u, int& m0, int& n0, int& c0, int& c1) {
     const int z = u / (mt * nt), r = u % (mt * nt);
-    m0 = (r / nt) * OZ_TM;
-    n0 = (r % nt) * OZ_TN;
+    m0 = (mt <= nt ? r % mt : r / nt) * OZ_TM;
+    n0 = (mt <= nt ? r / mt : r % nt) * OZ_TN;
     c0 = z * a.cps;
     c1 = min(a.nchunks, c0 + a.cps);
     return z;
@@ -305,14 +403,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
     }
   } else {
-    // epilogue: warps 2..5 own tensor-memory lane quarters (warp % 4)
+    // epilogue: warps 2..5 own tensor-memory lane quarters (warp % 4). A pass
+    // value is an exact integer held in fp32; the passes of a unit are summed
+    // in a 64-bit fixed-point accumulator S with integer operations only. S
+    // lives in this CTA's slice of the workspace, laid out [column][row] so that
+    // a warp touches 32 consecutive rows, and is converted to fp64 once, after
+    // the unit's last pass.
     const int qw = warp % 4;
+    const int row = qw * 32 + lane;
+    longlong2* S = a.acc + (size_t)blockIdx.x * OZ_TM * OZ_TN + row;
     int i = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
       int m0, n0, c0, c1;
       const int z = unit_of(u, m0, n0, c0, c1);
-      const int m = m0 + qw * 32 + lane;
+      const int m = m0 + row;
       const int em = m < a.M ? a.ea[m] : 0;
       for (int c = c0; c < c1 && ok; ++c)
         for (int g = 0; g < a.G; ++g, ++i) {
@@ -322,29 +427,44 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const bool overwrite = (c == c0 && g == 0);
-          const int sh = em - 2 * OZ_P - OZ_W * g;
+          const bool first = (c == c0 && g == 0), last = (c == c1 - 1 && g == a.G - 1);
+          // weight of this group in S: 2^(base_shift - W g) units of the pass value
+          const int shift = a.base_shift - OZ_W * g;
           const uint32_t trow = tmem + (uint32_t)(b * 2 * OZ_TN) + ((uint32_t)(qw * 32) << 16);
           for (int cc = 0; cc < OZ_TN; cc += 32) {
             uint32_t rr[32], ri[32];
             tmem_ld32(trow + cc, rr);
             tmem_ld32(trow + OZ_TN + cc, ri);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (m >= a.M) continue;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int n = n0 + cc + j;
-              if (n >= a.N) continue;
-              const int e = sh + a.eb[n];
-              const double vr = ldexp((double)__uint_as_float(rr[j]), e);
-              const double vi = ldexp((double)__uint_as_float(ri[j]), e);
-              double2* dst = a.splits == 1 ? a.C + (long long)m * a.sCm + (long long)n * a.sCn
-                                           : a.part + ((long long)z * a.M + m) * (long long)a.N + n;
-              if (overwrite) {
-                *dst = make_double2(vr, vi);
-              } else {
-                const double2 old = *dst;
-                *dst = make_double2(old.x + vr, old.y + vi);
+            for (int h = 0; h < 32; h += 16) {
+              // the 16 previous sums first (independent loads in flight together)
+              longlong2 old[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                old[j] = first ? make_longlong2(0, 0) : S[(size_t)(cc + h + j) * OZ_TM];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const int col = cc + h + j;
+                long long vr = (long long)__float2int_rn(__uint_as_float(rr[h + j]));
+                long long vi = (long long)__float2int_rn(__uint_as_float(ri[h + j]));
+                vr = (shift >= 0 ? vr * (1LL << shift) : (vr >> -shift)) + old[j].x;
+                vi = (shift >= 0 ? vi * (1LL << shift) : (vi >> -shift)) + old[j].y;
+                if (!last) {
+                  S[(size_t)col * OZ_TM] = make_longlong2(vr, vi);
+                } else if (m < a.M && n0 + col < a.N) {
+                  const int n = n0 + col;
+                  const int en = a.eb[n];
+                  double2* dst = a.splits == 1 ? a.C + (long long)m * a.sCm + (long long)n * a.sCn
+                                               : a.part + ((long long)z * a.M + m) * (long long)a.N + n;
+                  if (em == OZ_NONFINITE || en == OZ_NONFINITE) {
+                    *dst = make_double2(__longlong_as_double(0x7FF8000000000000LL),
+                                        __longlong_as_double(0x7FF8000000000000LL));
+                  } else {
+                    const int e2 = em + en - 2 * OZ_P - a.base_shift;
+                    *dst = make_double2(fixed_to_f64(vr, e2), fixed_to_f64(vi, e2));
+                  }
+                }
               }
             }
           }
@@ -374,8 +494,9 @@ int grid_of(long long n, int per_block, int sms) {
 }
 
 struct OzPlan {
-  int k_tiles, nchunks, cps, splits;
-  size_t a_bytes, b_bytes, e_bytes, p_bytes;
+  int k_tiles, nchunks, cps, splits, grid, base_shift;
+  size_t a_bytes, b_bytes, e_bytes, p_bytes, s_bytes;
+  size_t total() const { return a_bytes + b_bytes + e_bytes + p_bytes + s_bytes; }
 };
 
 OzPlan plan(int M, int N, int K, int G, int num_sms) {
@@ -392,6 +513,14 @@ OzPlan plan(int M, int N, int K, int G, int num_sms) {
   p.b_bytes = al256((size_t)2 * G * N * kp * 2);
   p.e_bytes = al256((size_t)(M + N) * sizeof(int));
   p.p_bytes = p.splits > 1 ? al256((size_t)p.splits * M * N * 16) : 0;
+  const long long units = (long long)((M + OZ_TM - 1) / OZ_TM) * ((N + OZ_TN - 1) / OZ_TN) * p.splits;
+  p.grid = (int)std::min<long long>(units, (long long)num_sms);
+  p.s_bytes = al256((size_t)p.grid * OZ_TM * OZ_TN * sizeof(longlong2));
+  // |pass value| <= 2^24 and sum_g 2^-W g < 1.008: cps chunks stay below
+  // 2^(base_shift + 24 + log2 cps + 0.02) <= 2^62.02 < 2^63
+  int lg = 0;
+  while ((1 << lg) < p.cps) ++lg;
+  p.base_shift = 38 - lg;
   return p;
 }
 
@@ -419,7 +548,7 @@ int oz_max_slices() { return OZ_MAX_SLICES; }
 size_t ozgemm64_workspace(const GemmDesc& g, int slices, int num_sms) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0 || slices < 1 || slices > OZ_MAX_SLICES) return 0;
   const OzPlan p = plan(g.M, g.N, g.K, slices, num_sms);
-  return p.a_bytes + p.b_bytes + p.e_bytes + p.p_bytes;
+  return p.total();
 }
 
 int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws_bytes, int* err) {
@@ -436,7 +565,7 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
     attr_done = true;
   }
   const OzPlan p = plan(g.M, g.N, g.K, slices, L.num_sms);
-  if (!ws || !err || ws_bytes < p.a_bytes + p.b_bytes + p.e_bytes + p.p_bytes) return TEVO_ESHAPE;
+  if (!ws || !err || ws_bytes < p.total()) return TEVO_ESHAPE;
   char* w = static_cast<char*>(ws);
   __nv_bfloat16* da = reinterpret_cast<__nv_bfloat16*>(w);
   w += p.a_bytes;
@@ -446,6 +575,8 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
   int* eb = ea + g.M;
   w += p.e_bytes;
   double2* part = p.splits > 1 ? reinterpret_cast<double2*>(w) : nullptr;
+  w += p.p_bytes;
+  longlong2* acc = reinterpret_cast<longlong2*>(w);
   const long long kp = pad8(g.K);
   // A(m, k) at A + m sAm + k sAk; B(k, n) at B + k sBk + n sBn, read as rows n
   OzSplit sa{static_cast<const double2*>(g.A), g.sAm, g.sAk, g.M, g.K, g.conjA, slices, da, (long long)g.M * kp, kp,
@@ -480,10 +611,12 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
   a.sCm = g.sCm;
   a.sCn = g.sCn;
   a.part = part;
+  a.acc = acc;
+  a.base_shift = p.base_shift;
   a.err = err;
   const long long units = (long long)((g.M + OZ_TM - 1) / OZ_TM) * ((g.N + OZ_TN - 1) / OZ_TN) * p.splits;
   if (units > (1LL << 30)) return TEVO_ESHAPE;
-  dim3 grid((unsigned)std::min<long long>(units, (long long)L.num_sms));
+  dim3 grid((unsigned)p.grid);
   const double useful = 8.0 * (double)g.M * g.N * g.K;
   const int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_GEMMOZ, useful, 16.0 * ((double)g.M * g.K + (double)g.N * g.K +
                                                                                    (double)g.M * g.N))

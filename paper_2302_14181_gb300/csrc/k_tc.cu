@@ -241,10 +241,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t bytesA = a.planes * TM * KCB, bytesB = a.planes * TN * KCB;
 
   // tile t -> (split z, row tile y, column tile x) and its K-tile range
+  // the shorter tile dimension runs fastest, so CTAs that run together share
+  // the tiles of the longer operand (read once from DRAM, then from L2)
   auto tile_of = [&](int t, int& m0, int& n0, int& kt0, int& kt1) {
     const int z = t / (mt * nt), r = t % (mt * nt);
-    m0 = (r / nt) * TM;
-    n0 = (r % nt) * TN;
+    m0 = (mt <= nt ? r % mt : r / nt) * TM;
+    n0 = (mt <= nt ? r / mt : r % nt) * TN;
     kt0 = z * a.tiles_per_split;
     kt1 = min(a.k_tiles, kt0 + a.tiles_per_split);
     if (kt1 < kt0) kt1 = kt0;

@@ -98,6 +98,23 @@ def test_rows_of_very_different_magnitude(ctx):
     assert (np.abs(got - ref) <= 9 * 2.0 ** -49 * row_scale).all()
 
 
+def test_nonfinite_rows_give_nan_outputs(ctx):
+    """Digits of a row holding NaN or Inf are not formed; the entries that row
+    touches come out NaN (so the evolution's non-finite check still fires)."""
+    rng = np.random.default_rng(13)
+    A = rng.standard_normal((40, 64)) + 1j * rng.standard_normal((40, 64))
+    B = rng.standard_normal((30, 64)) + 1j * rng.standard_normal((30, 64))
+    A[3, 7] = np.nan
+    B[5, 2] = np.inf
+    got = gemm(ctx, tv.OZAKI, A, B)
+    bad = np.zeros(got.shape, bool)
+    bad[3, :] = True
+    bad[:, 5] = True
+    assert np.isnan(got[bad]).all()
+    ref = A @ B.T
+    assert np.abs(got[~bad] - ref[~bad]).max() <= bound(7, A[np.isfinite(A).all(1)], B[np.isfinite(B).all(1)])
+
+
 def test_bad_ozaki_flags_are_rejected(ctx):
     A = np.ones((4, 4), np.complex128)
     a = torch.from_numpy(A).cuda()
