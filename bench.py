@@ -35,9 +35,9 @@ METRIC = "W^(N)·MPS fit sweeps/s & TFLOP/s vs peak at ≤1e-6 obs error, mixed 
 WORKLOAD = "lri_L100_N3_D256"
 PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3,
         "tc-tf32": 0x101, "tc-tf32x3": 0x102, "tc-bf16x3": 0x103,
-        # fp64 contractions as Ozaki-scheme GEMMs (7 digit slices) on the tensor cores
+        # fp64 contractions as Ozaki-scheme GEMMs (8 digit slices) on the tensor cores
         "fp64+oz": 0x200, "tf32+oz": 0x201, "tf32x3+oz": 0x202, "bf16x3+oz": 0x203}
-OZ_SLICES = 7
+OZ_SLICES = 8
 OZ_PAIRS = OZ_SLICES * (OZ_SLICES + 1) // 2  # digit-slice products per complex product
 # fp64 issue rate on GB300: 2 DFMA per clock per SM (152 SMs, 2070 MHz max SM clock)
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
@@ -182,7 +182,7 @@ def dtype_of(form):
     if form == "fp64":
         return "c128"
     if form == "fp64+oz":
-        return "c128 in/out; contractions as exact bf16 digit-slice products (Ozaki, 7 slices), fp64 sums"
+        return "c128 in/out; contractions as exact bf16 digit-slice products (Ozaki, 8 slices), fixed-point sums"
     base = form.replace("tc-", "").replace("+oz", "")
     if form.startswith("tc-"):
         return f"{base} contractions + c128 QR"

@@ -195,7 +195,9 @@ int make_T64(tevo_mps s, const StepDims& k, const z64* El, const z64* A, const z
   // G1: X[(p w), (s' b)] = El[(p w), a] A[a, (s' b)]
   TRY(gemm(s, gd(El, 0, k.Da, 1, A, 0, (long long)k.d * k.Db, 1, s->X.p, 0, (long long)k.d * k.Db, 1,
                  k.Dp * k.wl, k.d * k.Db, k.Da, 1)));
-  if (sidx && sidx->p) {
+  // the sparse G2 runs on the fp64 pipe; with the Ozaki contractions the dense
+  // G2 (one batched GEMM with the MPO operand shared) is faster on the tensor cores
+  if (sidx && sidx->p && s->oz_slices == 0) {
     const int R = k.d * k.wr;
     const int* rp = static_cast<const int*>(sidx->p);
     int e = zsparse_g2(launch_of(s->ctx), zp(s->X), zp(s->T), rp, rp + R + 1, static_cast<const z64*>(sval->p), R,
@@ -765,7 +767,7 @@ int oz_slices_of(int precision) {
   if (!(precision & TEVO_OZAKI)) return (precision >> 12) ? -1 : 0;
   const int g = (precision >> 12) & 0xF;
   if (precision >> 16) return -1;
-  if (g == 0) return 7;
+  if (g == 0) return 8;
   return g <= oz_max_slices() ? g : -1;
 }
 

@@ -66,8 +66,10 @@ constexpr int OZ_SMEM_BYTES = OZ_NSTAGE * OZ_STAGE_BYTES + 1024 /*align*/ + 256 
 constexpr int OZ_THREADS = 192;
 
 // one operand to cut into digit slices: element (r, k) of R x K at
-// src[r * sR + k * sK] (conjugated when conj), digit planes written to
-// dst[p * plane_stride + r * row_pitch + k], row exponents to exps[r]
+// src[(r / R2) * sR1 + (r % R2) * sR + k * sK] (conjugated when conj), digit
+// planes written to dst[p * plane_stride + r * row_pitch + k], the row maxima
+// of the magnitude bit patterns to maxbits[r] (zeroed before), the row
+// exponents to exps[r]
 struct OzSplit {
   const double2* src;
   long long sR, sK;
@@ -77,15 +79,24 @@ struct OzSplit {
   __nv_bfloat16* dst;
   long long plane_stride, row_pitch;
   int* exps;
+  unsigned long long* maxbits;
+  int R2;
+  long long sR1;
 };
+
+__device__ __forceinline__ long long row_offset(const OzSplit& o, long long r) {
+  return (r / o.R2) * o.sR1 + (r % o.R2) * o.sR;
+}
 
 struct OzArgs {
   int M, N, G;
   int k_tiles, nchunks, cps, splits;  // K-tiles of 32, exact chunks, chunks per split
   const int* ea;                      // row exponents of A (M) and of B (N)
   const int* eb;
-  double2* C;  // output when splits == 1
+  double2* C;  // output when splits == 1: (m, n) at m sCm + (n / N2) sCn1 + (n % N2) sCn
   long long sCm, sCn;
+  int N2;
+  long long sCn1;
   double2* part;  // [splits][M][N] when splits > 1
   longlong2* acc;  // fixed-point sums: [CTA][column][row] of one 128 x 128 tile per CTA
   int base_shift;  // S unit: 2^-base_shift of a group-0 pass value
@@ -175,14 +186,20 @@ __host__ __device__ inline double fixed_to_f64(long long s, int e2) {
 #endif
 }
 
-// one warp per row (K contiguous or both strides general)
-__global__ void oz_rowexp_warp_kernel(OzSplit o) {
-  const int warps = blockDim.x / 32;
+// row maxima of the magnitude bit patterns: a warp reduces one row over a
+// segment of 256 K-indices (K contiguous or general strides) and merges it
+// with atomicMax, so long rows are spread over many warps
+__global__ void oz_rowmax_warp_kernel(OzSplit o, int nseg) {
   const int lane = threadIdx.x % 32;
-  for (long long r = (long long)blockIdx.x * warps + threadIdx.x / 32; r < o.R; r += (long long)gridDim.x * warps) {
+  const long long nwarps = (long long)o.R * nseg;
+  for (long long w = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < nwarps;
+       w += (long long)gridDim.x * (blockDim.x / 32)) {
+    const long long r = w / nseg;
+    const int k0 = int(w % nseg) * 256;
+    const double2* src = o.src + row_offset(o, r);
     unsigned long long mx = 0;
-    for (int k = lane; k < o.K; k += 32) {
-      const unsigned long long v = mag_bits(o.src[r * o.sR + (long long)k * o.sK]);
+    for (int k = k0 + lane; k < min(o.K, k0 + 256); k += 32) {
+      const unsigned long long v = mag_bits(src[(long long)k * o.sK]);
       mx = v > mx ? v : mx;
     }
 #pragma unroll
@@ -190,19 +207,28 @@ __global__ void oz_rowexp_warp_kernel(OzSplit o) {
       const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, off);
       mx = v > mx ? v : mx;
     }
-    if (lane == 0) o.exps[r] = row_exponent_bits(mx);
+    if (lane == 0 && mx) atomicMax(o.maxbits + r, mx);
   }
 }
 
-// one thread per row (rows contiguous: consecutive lanes read consecutive rows)
-__global__ void oz_rowexp_lane_kernel(OzSplit o) {
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < o.R; r += (long long)gridDim.x * blockDim.x) {
+// the same when rows are contiguous: a warp covers 32 consecutive rows (one per
+// lane) over a segment of 64 K-indices
+__global__ void oz_rowmax_lane_kernel(OzSplit o, int nseg) {
+  const long long nrow32 = ((long long)o.R + 31) / 32;
+  const long long nwarps = nrow32 * nseg;
+  const int lane = threadIdx.x % 32;
+  for (long long w = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < nwarps;
+       w += (long long)gridDim.x * (blockDim.x / 32)) {
+    const long long r = (w / nseg) * 32 + lane;
+    const int k0 = int(w % nseg) * 64;
+    if (r >= o.R) continue;
+    const double2* src = o.src + row_offset(o, r);
     unsigned long long mx = 0;
-    for (int k = 0; k < o.K; ++k) {
-      const unsigned long long v = mag_bits(o.src[r * o.sR + (long long)k * o.sK]);
+    for (int k = k0; k < min(o.K, k0 + 64); ++k) {
+      const unsigned long long v = mag_bits(src[(long long)k * o.sK]);
       mx = v > mx ? v : mx;
     }
-    o.exps[r] = row_exponent_bits(mx);
+    if (mx) atomicMax(o.maxbits + r, mx);
   }
 }
 
@@ -217,7 +243,7 @@ __global__ void oz_slice_kernel(OzSplit o) {
     const int rr = ROWS_CONTIG ? threadIdx.x : i, kk = ROWS_CONTIG ? i : threadIdx.x;
     const int r = r0 + rr, k = k0 + kk;
     double2 v = make_double2(0.0, 0.0);
-    if (r < o.R && k < o.K) v = o.src[(long long)r * o.sR + (long long)k * o.sK];
+    if (r < o.R && k < o.K) v = o.src[row_offset(o, r) + (long long)k * o.sK];
     if (o.conj) v.y = -v.y;
     tile[rr][kk] = v;
   }
@@ -226,7 +252,8 @@ __global__ void oz_slice_kernel(OzSplit o) {
     const int r = r0 + i, k = k0 + threadIdx.x;
     if (r >= o.R || k >= o.K) continue;
     const double2 v = tile[i][threadIdx.x];
-    const int e = o.exps[r];
+    const int e = row_exponent_bits(o.maxbits[r]);
+    if (k0 == 0 && threadIdx.x == 0) o.exps[r] = e;
     __nv_bfloat16* dst = o.dst + (long long)r * o.row_pitch + k;
     // greedy digits of the fixed-point value, most significant first: digit s
     // is the nearest integer (ties to even) to the remainder in units of 2^q,
@@ -252,7 +279,7 @@ __global__ void oz_slice_kernel(OzSplit o) {
 
 // fixed-order sum of the fp64 split partials into the strided output
 __global__ void oz_reduce_kernel(const double2* P, int splits, int M, int N, double2* C, long long sCm,
-                                 long long sCn) {
+                                 long long sCn, int N2, long long sCn1) {
   const long long total = (long long)M * N;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -263,7 +290,7 @@ __global__ void oz_reduce_kernel(const double2* P, int splits, int M, int N, dou
       re += v.x;
       im += v.y;
     }
-    C[m * sCm + n * sCn] = make_double2(re, im);
+    C[m * sCm + (long long)(n / N2) * sCn1 + (long long)(n % N2) * sCn] = make_double2(re, im);
   }
 }
 
@@ -455,7 +482,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 } else if (m < a.M && n0 + col < a.N) {
                   const int n = n0 + col;
                   const int en = a.eb[n];
-                  double2* dst = a.splits == 1 ? a.C + (long long)m * a.sCm + (long long)n * a.sCn
+                  double2* dst = a.splits == 1 ? a.C + (long long)m * a.sCm + (long long)(n / a.N2) * a.sCn1 +
+                                                     (long long)(n % a.N2) * a.sCn
                                                : a.part + ((long long)z * a.M + m) * (long long)a.N + n;
                   if (em == OZ_NONFINITE || en == OZ_NONFINITE) {
                     *dst = make_double2(__longlong_as_double(0x7FF8000000000000LL),
@@ -511,7 +539,7 @@ OzPlan plan(int M, int N, int K, int G, int num_sms) {
   const long long kp = pad8(K);
   p.a_bytes = al256((size_t)2 * G * M * kp * 2);
   p.b_bytes = al256((size_t)2 * G * N * kp * 2);
-  p.e_bytes = al256((size_t)(M + N) * sizeof(int));
+  p.e_bytes = al256((size_t)(M + N) * (sizeof(int) + sizeof(unsigned long long)));
   p.p_bytes = p.splits > 1 ? al256((size_t)p.splits * M * N * 16) : 0;
   const long long units = (long long)((M + OZ_TM - 1) / OZ_TM) * ((N + OZ_TN - 1) / OZ_TN) * p.splits;
   p.grid = (int)std::min<long long>(units, (long long)num_sms);
@@ -525,11 +553,16 @@ OzPlan plan(int M, int N, int K, int G, int num_sms) {
 }
 
 int split_operand(const Launch& L, const OzSplit& o) {
+  if (cudaMemsetAsync(o.maxbits, 0, sizeof(unsigned long long) * (size_t)o.R, L.stream) != cudaSuccess)
+    return TEVO_ECUDA;
   const bool rows_contig = o.sR == 1 && o.sK != 1;
-  if (rows_contig)
-    oz_rowexp_lane_kernel<<<grid_of(o.R, 256, L.num_sms), 256, 0, L.stream>>>(o);
-  else
-    oz_rowexp_warp_kernel<<<grid_of((long long)o.R * 32, 256, L.num_sms), 256, 0, L.stream>>>(o);
+  if (rows_contig) {
+    const int nseg = (o.K + 63) / 64;
+    oz_rowmax_lane_kernel<<<grid_of(((long long)o.R + 31) / 32 * nseg * 32, 256, L.num_sms), 256, 0, L.stream>>>(o, nseg);
+  } else {
+    const int nseg = (o.K + 255) / 256;
+    oz_rowmax_warp_kernel<<<grid_of((long long)o.R * nseg * 32, 256, L.num_sms), 256, 0, L.stream>>>(o, nseg);
+  }
   ++*L.launches;
   if ((o.R + 31) / 32 > 65535) return TEVO_ESHAPE;
   dim3 grid((o.K + 31) / 32, (o.R + 31) / 32), block(32, 8);
@@ -545,15 +578,22 @@ int split_operand(const Launch& L, const OzSplit& o) {
 
 int oz_max_slices() { return OZ_MAX_SLICES; }
 
+// a batch with a shared A operand is one GEMM over the batch-extended N
+static long long total_n(const GemmDesc& g) { return (long long)g.N * std::max(1, g.batch); }
+
 size_t ozgemm64_workspace(const GemmDesc& g, int slices, int num_sms) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0 || slices < 1 || slices > OZ_MAX_SLICES) return 0;
-  const OzPlan p = plan(g.M, g.N, g.K, slices, num_sms);
+  if (g.batch > 1 && g.sAb != 0) return 0;
+  if (total_n(g) > (1LL << 30)) return 0;
+  const OzPlan p = plan(g.M, (int)total_n(g), g.K, slices, num_sms);
   return p.total();
 }
 
 int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws_bytes, int* err) {
-  if (g.batch != 1 || g.conjB || g.alpha_re != 1.0 || g.alpha_im != 0.0 || g.beta_re != 0.0 || g.beta_im != 0.0)
+  if (g.batch < 1 || (g.batch > 1 && g.sAb != 0) || g.conjB || g.alpha_re != 1.0 || g.alpha_im != 0.0 ||
+      g.beta_re != 0.0 || g.beta_im != 0.0 || total_n(g) > (1LL << 30))
     return TEVO_EUNSUPPORTED;
+  const int Nt = (int)total_n(g);
   if (slices < 1 || slices > OZ_MAX_SLICES) return TEVO_EINVAL;
   if (g.M <= 0 || g.N <= 0) return 0;
   if (g.K <= 0) return TEVO_EUNSUPPORTED;
@@ -564,14 +604,16 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
       return TEVO_ECUDA;
     attr_done = true;
   }
-  const OzPlan p = plan(g.M, g.N, g.K, slices, L.num_sms);
+  const OzPlan p = plan(g.M, Nt, g.K, slices, L.num_sms);
   if (!ws || !err || ws_bytes < p.total()) return TEVO_ESHAPE;
   char* w = static_cast<char*>(ws);
   __nv_bfloat16* da = reinterpret_cast<__nv_bfloat16*>(w);
   w += p.a_bytes;
   __nv_bfloat16* db = reinterpret_cast<__nv_bfloat16*>(w);
   w += p.b_bytes;
-  int* ea = reinterpret_cast<int*>(w);
+  unsigned long long* mxa = reinterpret_cast<unsigned long long*>(w);
+  unsigned long long* mxb = mxa + g.M;
+  int* ea = reinterpret_cast<int*>(mxb + Nt);
   int* eb = ea + g.M;
   w += p.e_bytes;
   double2* part = p.splits > 1 ? reinterpret_cast<double2*>(w) : nullptr;
@@ -580,10 +622,12 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
   const long long kp = pad8(g.K);
   // A(m, k) at A + m sAm + k sAk; B(k, n) at B + k sBk + n sBn, read as rows n
   OzSplit sa{static_cast<const double2*>(g.A), g.sAm, g.sAk, g.M, g.K, g.conjA, slices, da, (long long)g.M * kp, kp,
-             ea};
-  OzSplit sb{static_cast<const double2*>(g.B), g.sBn, g.sBk, g.N, g.K, 0, slices, db, (long long)g.N * kp, kp, eb};
+             ea, mxa, g.M, 0};
+  // rows of B: (batch b, n) at b sBb + n sBn
+  OzSplit sb{static_cast<const double2*>(g.B), g.sBn, g.sBk, Nt, g.K, 0, slices, db, (long long)Nt * kp, kp, eb,
+             mxb, g.N, g.sBb};
   const int pr_split = L.prof ? L.prof->begin(L.stream, TEVO_PROF_OZSPLIT, 0.0,
-                                              (16.0 + 4.0 * slices) * ((double)g.M + g.N) * g.K)
+                                              (16.0 + 4.0 * slices) * ((double)g.M + Nt) * g.K)
                               : -1;
   int e = split_operand(L, sa);
   if (!e) e = split_operand(L, sb);
@@ -591,7 +635,7 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
   if (e) return e;
 
   TcOperand oa{da, 2, 2 * slices, (long long)g.M * kp, g.M, kp, g.K, 1, kp};
-  TcOperand ob{db, 2, 2 * slices, (long long)g.N * kp, g.N, kp, g.K, 1, kp};
+  TcOperand ob{db, 2, 2 * slices, (long long)Nt * kp, Nt, kp, g.K, 1, kp};
   CUtensorMap ma, mb;
   e = tc_make_map(&ma, oa, OZ_TM, 2);
   if (!e) e = tc_make_map(&mb, ob, OZ_TN, 2);
@@ -599,7 +643,7 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
   OzArgs a;
   std::memset(&a, 0, sizeof(a));
   a.M = g.M;
-  a.N = g.N;
+  a.N = Nt;
   a.G = slices;
   a.k_tiles = p.k_tiles;
   a.nchunks = p.nchunks;
@@ -610,22 +654,24 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
   a.C = static_cast<double2*>(g.C);
   a.sCm = g.sCm;
   a.sCn = g.sCn;
+  a.N2 = g.N;
+  a.sCn1 = g.sCb;
   a.part = part;
   a.acc = acc;
   a.base_shift = p.base_shift;
   a.err = err;
-  const long long units = (long long)((g.M + OZ_TM - 1) / OZ_TM) * ((g.N + OZ_TN - 1) / OZ_TN) * p.splits;
+  const long long units = (long long)((g.M + OZ_TM - 1) / OZ_TM) * ((Nt + OZ_TN - 1) / OZ_TN) * p.splits;
   if (units > (1LL << 30)) return TEVO_ESHAPE;
   dim3 grid((unsigned)p.grid);
-  const double useful = 8.0 * (double)g.M * g.N * g.K;
-  const int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_GEMMOZ, useful, 16.0 * ((double)g.M * g.K + (double)g.N * g.K +
-                                                                                   (double)g.M * g.N))
+  const double useful = 8.0 * (double)g.M * Nt * g.K;
+  const int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_GEMMOZ, useful,
+                                        16.0 * ((double)g.M * g.K + (double)Nt * g.K + (double)g.M * Nt))
                         : -1;
   oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, L.stream>>>(ma, mb, a);
   ++*L.launches;
   if (p.splits > 1) {
-    oz_reduce_kernel<<<grid_of((long long)g.M * g.N, 256, L.num_sms), 256, 0, L.stream>>>(
-        part, p.splits, g.M, g.N, static_cast<double2*>(g.C), g.sCm, g.sCn);
+    oz_reduce_kernel<<<grid_of((long long)g.M * Nt, 256, L.num_sms), 256, 0, L.stream>>>(
+        part, p.splits, g.M, Nt, static_cast<double2*>(g.C), g.sCm, g.sCn, g.N, g.sCb);
     ++*L.launches;
   }
   if (L.prof) L.prof->end(L.stream, pr);
