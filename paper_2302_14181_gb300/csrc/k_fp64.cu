@@ -517,7 +517,8 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
     // the R part of column k (rows above k) for qr64_extract_r
     const double2* col = cols + (size_t)(k / G) * m;
     for (int r = threadIdx.x; r < k; r += blockDim.x) A[(long long)k * m + r] = col[r];
-    __threadfence();  // each thread's stores, before the release below
+    // the block barrier orders every thread's stores before thread 0's device
+    // fence and release below (one fence per block, not one per thread)
     __syncthreads();
     if (threadIdx.x == 0) {
       tau[k] = s_tau[k & 1];

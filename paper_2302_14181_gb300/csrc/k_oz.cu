@@ -232,47 +232,62 @@ __global__ void oz_rowmax_lane_kernel(OzSplit o, int nseg) {
   }
 }
 
+// greedy digits of one fixed-point value, most significant first: digit s is
+// the nearest integer (ties to even) to the remainder in units of 2^q,
+// q = W (G - 1 - s); integer arithmetic only
+__device__ __forceinline__ long long next_digit(long long& x, int q) {
+  long long d = x;
+  if (q > 0) d = (x + ((1LL << (q - 1)) - 1) + ((x >> q) & 1)) >> q;
+  x -= d * (1LL << q);
+  return d;
+}
+
 // digit planes [2G][R][row_pitch] (plane 2s = Re of slice s, 2s+1 = Im) of a
-// 32 x 32 tile, staged in shared memory so that both the fp64 reads (along the
-// contiguous source index) and the bf16 writes (along K) are coalesced
+// 32-row x 64-K tile, staged in shared memory so that the fp64 reads (along the
+// contiguous source index) are coalesced; each thread then forms the digits of
+// two neighbouring K entries and writes them as one 4-byte bf16 pair per plane
 template <bool ROWS_CONTIG>
 __global__ void oz_slice_kernel(OzSplit o) {
-  __shared__ double2 tile[32][33];
-  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
-  for (int i = threadIdx.y; i < 32; i += 8) {
-    const int rr = ROWS_CONTIG ? threadIdx.x : i, kk = ROWS_CONTIG ? i : threadIdx.x;
-    const int r = r0 + rr, k = k0 + kk;
-    double2 v = make_double2(0.0, 0.0);
-    if (r < o.R && k < o.K) v = o.src[row_offset(o, r) + (long long)k * o.sK];
-    if (o.conj) v.y = -v.y;
-    tile[rr][kk] = v;
+  __shared__ double2 tile[32][65];
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+  if (ROWS_CONTIG) {
+    for (int kk = threadIdx.y; kk < 64; kk += 8) {
+      const int r = r0 + threadIdx.x, k = k0 + kk;
+      double2 v = make_double2(0.0, 0.0);
+      if (r < o.R && k < o.K) v = o.src[row_offset(o, r) + (long long)k * o.sK];
+      if (o.conj) v.y = -v.y;
+      tile[threadIdx.x][kk] = v;
+    }
+  } else {
+    for (int i = threadIdx.y; i < 32; i += 8)
+      for (int h = 0; h < 64; h += 32) {
+        const int r = r0 + i, k = k0 + h + threadIdx.x;
+        double2 v = make_double2(0.0, 0.0);
+        if (r < o.R && k < o.K) v = o.src[row_offset(o, r) + (long long)k * o.sK];
+        if (o.conj) v.y = -v.y;
+        tile[i][h + threadIdx.x] = v;
+      }
   }
   __syncthreads();
+  const int F = OZ_P + OZ_W * (o.G - 1);
   for (int i = threadIdx.y; i < 32; i += 8) {
-    const int r = r0 + i, k = k0 + threadIdx.x;
+    const int r = r0 + i, k = k0 + 2 * threadIdx.x;
     if (r >= o.R || k >= o.K) continue;
-    const double2 v = tile[i][threadIdx.x];
     const int e = row_exponent_bits(o.maxbits[r]);
     if (k0 == 0 && threadIdx.x == 0) o.exps[r] = e;
-    __nv_bfloat16* dst = o.dst + (long long)r * o.row_pitch + k;
-    // greedy digits of the fixed-point value, most significant first: digit s
-    // is the nearest integer (ties to even) to the remainder in units of 2^q,
-    // q = W (G - 1 - s); integer arithmetic only
-    const int F = OZ_P + OZ_W * (o.G - 1);
-    long long xr = e == OZ_NONFINITE ? 0 : to_fixed(v.x, e, F);
-    long long xi = e == OZ_NONFINITE ? 0 : to_fixed(v.y, e, F);
+    const bool fin = e != OZ_NONFINITE;
+    // entries past K are zero (tile padding), so the pair never needs a tail case
+    const double2 v0 = tile[i][2 * threadIdx.x], v1 = tile[i][2 * threadIdx.x + 1];
+    long long x0r = fin ? to_fixed(v0.x, e, F) : 0, x0i = fin ? to_fixed(v0.y, e, F) : 0;
+    long long x1r = fin ? to_fixed(v1.x, e, F) : 0, x1i = fin ? to_fixed(v1.y, e, F) : 0;
+    __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(o.dst + (long long)r * o.row_pitch + k);
+    const long long ps2 = o.plane_stride / 2;  // plane stride in bf16 pairs (even: rows are padded to 8)
     for (int s = 0; s < o.G; ++s) {
       const int q = OZ_W * (o.G - 1 - s);
-      long long dr = xr, di = xi;
-      if (q > 0) {
-        const long long bias = (1LL << (q - 1)) - 1;
-        dr = (xr + bias + ((xr >> q) & 1)) >> q;
-        di = (xi + bias + ((xi >> q) & 1)) >> q;
-      }
-      xr -= dr * (1LL << q);
-      xi -= di * (1LL << q);
-      dst[(long long)(2 * s) * o.plane_stride] = __float2bfloat16_rn((float)dr);
-      dst[(long long)(2 * s + 1) * o.plane_stride] = __float2bfloat16_rn((float)di);
+      const float d0r = (float)next_digit(x0r, q), d1r = (float)next_digit(x1r, q);
+      const float d0i = (float)next_digit(x0i, q), d1i = (float)next_digit(x1i, q);
+      dst[(long long)(2 * s) * ps2] = __floats2bfloat162_rn(d0r, d1r);
+      dst[(long long)(2 * s + 1) * ps2] = __floats2bfloat162_rn(d0i, d1i);
     }
   }
 }
@@ -565,7 +580,7 @@ int split_operand(const Launch& L, const OzSplit& o) {
   }
   ++*L.launches;
   if ((o.R + 31) / 32 > 65535) return TEVO_ESHAPE;
-  dim3 grid((o.K + 31) / 32, (o.R + 31) / 32), block(32, 8);
+  dim3 grid((o.K + 63) / 64, (o.R + 31) / 32), block(32, 8);
   if (rows_contig)
     oz_slice_kernel<true><<<grid, block, 0, L.stream>>>(o);
   else
