@@ -31,7 +31,7 @@
 //
 // The tensor-core schedule is that of the plain complex GEMM (k_tc.cu): a
 // persistent CTA per SM, a TMA producer warp, one thread issuing tcgen05.mma,
-// four epilogue warps, two tensor-memory accumulator buffers (a pass drains
+// eight epilogue warps (two per tensor-memory lane quarter), two tensor-memory accumulator buffers (a pass drains
 // while the next accumulates). A stage holds the (re, im) planes of one A slice
 // and of one B slice for 32 K-indices; it feeds four real MMAs per 16 K:
 //   Re += Ar Br - Ai Bi,   Im += Ar Bi + Ai Br.
@@ -63,7 +63,14 @@ constexpr int OZ_A_BYTES = 2 * OZ_TM * OZ_KCB;  // re, im planes of one slice: 1
 constexpr int OZ_B_BYTES = 2 * OZ_TN * OZ_KCB;
 constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
 constexpr int OZ_SMEM_BYTES = OZ_NSTAGE * OZ_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int OZ_THREADS = 192;
+#ifndef OZ_EPILOGUE_WARPS
+#define OZ_EPILOGUE_WARPS 8
+#endif
+// epilogue warps: one or two per tensor-memory lane quarter (4 or 8), each on
+// all or half of the tile's columns
+constexpr int OZ_EPI_WARPS = OZ_EPILOGUE_WARPS;
+static_assert(OZ_EPI_WARPS == 4 || OZ_EPI_WARPS == 8, "epilogue warps");
+constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
 
 // one operand to cut into digit slices: element (r, k) of R x K at
 // src[(r / R2) * sR1 + (r % R2) * sR + k * sK] (conjugated when conj), digit
@@ -102,6 +109,15 @@ struct OzArgs {
   int base_shift;  // S unit: 2^-base_shift of a group-0 pass value
   int* err;
 };
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
 
 // row exponent marking a row that holds a NaN or an infinity: its digits are
 // zero and every output entry it touches is NaN
@@ -149,7 +165,10 @@ __device__ __forceinline__ long long to_fixed(double x, int e, int F) {
 // s * 2^e2 in fp64, rounded to nearest (ties to even), assembled from the
 // binary64 fields with integer operations; results outside the normal range
 // take the conversion instruction and an exact power-of-two scaling instead
-__host__ __device__ inline double fixed_to_f64(long long s, int e2) {
+#ifdef __CUDA_ARCH__
+__noinline__
+#endif
+__host__ __device__ double fixed_to_f64(long long s, int e2) {
   if (s == 0) return 0.0;
   const unsigned long long neg = (unsigned long long)s >> 63;
   const unsigned long long u = neg ? 0ull - (unsigned long long)s : (unsigned long long)s;
@@ -330,7 +349,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, 4);  // one arrival per epilogue warp
+      mbar_init(tempty0 + 8 * b, OZ_EPI_WARPS);  // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -445,13 +464,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
     }
   } else {
-    // epilogue: warps 2..5 own tensor-memory lane quarters (warp % 4). A pass
+    // epilogue: warps 2..9; warp w owns tensor-memory lane quarter w % 4 and half
+    // of the tile's columns. A pass
     // value is an exact integer held in fp32; the passes of a unit are summed
     // in a 64-bit fixed-point accumulator S with integer operations only. S
     // lives in this CTA's slice of the workspace, laid out [column][row] so that
     // a warp touches 32 consecutive rows, and is converted to fp64 once, after
     // the unit's last pass.
     const int qw = warp % 4;
+    const int c_lo = ((warp - 2) / 4) * (OZ_TN * 4 / OZ_EPI_WARPS);  // this warp's columns
+    const int c_hi = c_lo + OZ_TN * 4 / OZ_EPI_WARPS;
     const int row = qw * 32 + lane;
     longlong2* S = a.acc + (size_t)blockIdx.x * OZ_TM * OZ_TN + row;
     int i = 0;
@@ -473,40 +495,36 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           // weight of this group in S: 2^(base_shift - W g) units of the pass value
           const int shift = a.base_shift - OZ_W * g;
           const uint32_t trow = tmem + (uint32_t)(b * 2 * OZ_TN) + ((uint32_t)(qw * 32) << 16);
-          for (int cc = 0; cc < OZ_TN; cc += 32) {
-            uint32_t rr[32], ri[32];
-            tmem_ld32(trow + cc, rr);
-            tmem_ld32(trow + OZ_TN + cc, ri);
+          for (int cc = c_lo; cc < c_hi; cc += 16) {
+            uint32_t rr[16], ri[16];
+            tmem_ld16(trow + cc, rr);
+            tmem_ld16(trow + OZ_TN + cc, ri);
+            // the 16 previous sums (independent loads in flight together)
+            longlong2 old[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) old[j] = first ? make_longlong2(0, 0) : S[(size_t)(cc + j) * OZ_TM];
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int h = 0; h < 32; h += 16) {
-              // the 16 previous sums first (independent loads in flight together)
-              longlong2 old[16];
-#pragma unroll
-              for (int j = 0; j < 16; ++j)
-                old[j] = first ? make_longlong2(0, 0) : S[(size_t)(cc + h + j) * OZ_TM];
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const int col = cc + h + j;
-                long long vr = (long long)__float2int_rn(__uint_as_float(rr[h + j]));
-                long long vi = (long long)__float2int_rn(__uint_as_float(ri[h + j]));
-                vr = (shift >= 0 ? vr * (1LL << shift) : (vr >> -shift)) + old[j].x;
-                vi = (shift >= 0 ? vi * (1LL << shift) : (vi >> -shift)) + old[j].y;
-                if (!last) {
-                  S[(size_t)col * OZ_TM] = make_longlong2(vr, vi);
-                } else if (m < a.M && n0 + col < a.N) {
-                  const int n = n0 + col;
-                  const int en = a.eb[n];
-                  double2* dst = a.splits == 1 ? a.C + (long long)m * a.sCm + (long long)(n / a.N2) * a.sCn1 +
-                                                     (long long)(n % a.N2) * a.sCn
-                                               : a.part + ((long long)z * a.M + m) * (long long)a.N + n;
-                  if (em == OZ_NONFINITE || en == OZ_NONFINITE) {
-                    *dst = make_double2(__longlong_as_double(0x7FF8000000000000LL),
-                                        __longlong_as_double(0x7FF8000000000000LL));
-                  } else {
-                    const int e2 = em + en - 2 * OZ_P - a.base_shift;
-                    *dst = make_double2(fixed_to_f64(vr, e2), fixed_to_f64(vi, e2));
-                  }
+            for (int j = 0; j < 16; ++j) {
+              const int col = cc + j;
+              long long vr = (long long)__float2int_rn(__uint_as_float(rr[j]));
+              long long vi = (long long)__float2int_rn(__uint_as_float(ri[j]));
+              vr = (shift >= 0 ? vr * (1LL << shift) : (vr >> -shift)) + old[j].x;
+              vi = (shift >= 0 ? vi * (1LL << shift) : (vi >> -shift)) + old[j].y;
+              if (!last) {
+                S[(size_t)col * OZ_TM] = make_longlong2(vr, vi);
+              } else if (m < a.M && n0 + col < a.N) {
+                const int n = n0 + col;
+                const int en = a.eb[n];
+                double2* dst = a.splits == 1 ? a.C + (long long)m * a.sCm + (long long)(n / a.N2) * a.sCn1 +
+                                                   (long long)(n % a.N2) * a.sCn
+                                             : a.part + ((long long)z * a.M + m) * (long long)a.N + n;
+                if (em == OZ_NONFINITE || en == OZ_NONFINITE) {
+                  *dst = make_double2(__longlong_as_double(0x7FF8000000000000LL),
+                                      __longlong_as_double(0x7FF8000000000000LL));
+                } else {
+                  const int e2 = em + en - 2 * OZ_P - a.base_shift;
+                  *dst = make_double2(fixed_to_f64(vr, e2), fixed_to_f64(vi, e2));
                 }
               }
             }
