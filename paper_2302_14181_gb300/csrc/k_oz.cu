@@ -7,11 +7,10 @@
 // max_k max(|Re|, |Im|) < 2^e_r, and the scaled row (entries in (-1, 1)) is cut
 // into G digit slices
 //   x = 2^e_r * sum_s alpha_s * 2^-(P + W s) + rest,   |alpha_s| <= 2^P,
-// taken greedily with round-to-nearest (alpha_s = the remaining part in units of
-// 2^-(P + W s), rounded to the nearest integer), P = 6, W = 7 bits per slice,
+// taken as the balanced base-2^W digits of x 2^-e_r rounded to a fixed-point
+// integer of P + W (G - 1) fraction bits, P = 6, W = 7 bits per slice,
 // |rest| <= 2^(e_r - W G). Scaling and slicing work on the bit patterns with
-// integer operations (x 2^-e_r as a fixed-point integer of P + W (G - 1)
-// fraction bits); a row holding a NaN or an infinity gives NaN outputs.
+// integer operations; a row holding a NaN or an infinity gives NaN outputs.
 // The digits are integers of at most 7 significant bits, so they are exact in
 // bf16, their products (at most 2^12) are exact, and a sum of up to 4096 such
 // products is an integer below 2^24: exact in the fp32 accumulator of the
@@ -251,14 +250,15 @@ __global__ void oz_rowmax_lane_kernel(OzSplit o, int nseg) {
   }
 }
 
-// greedy digits of one fixed-point value, most significant first: digit s is
-// the nearest integer (ties to even) to the remainder in units of 2^q,
-// q = W (G - 1 - s); integer arithmetic only
-__device__ __forceinline__ long long next_digit(long long& x, int q) {
-  long long d = x;
-  if (q > 0) d = (x + ((1LL << (q - 1)) - 1) + ((x >> q) & 1)) >> q;
-  x -= d * (1LL << q);
-  return d;
+// balanced base-2^W digits of a fixed-point value X (|X| <= 2^F): with
+// U = X + C, C = 2^P sum_s 2^q_s (q_s = W (G - 1 - s)), digit s is the W-bit
+// field of U at q_s minus 2^P (the leading digit takes all bits above q_0), so
+// every digit lies in [-2^P, 2^P] and sum_s digit_s 2^q_s = X exactly
+__device__ __forceinline__ int digit_of(unsigned long long U, int s, int G) {
+  const int q = OZ_W * (G - 1 - s);
+  const unsigned long long f = s == 0 ? (U >> q) : ((U >> q) & ((1ull << OZ_W) - 1ull));
+  const int d = (int)min(f, (unsigned long long)(2 << OZ_P)) - (1 << OZ_P);  // the min never binds for |X| <= 2^F
+  return d < -(1 << OZ_P) ? -(1 << OZ_P) : d;
 }
 
 // digit planes [2G][R][row_pitch] (plane 2s = Re of slice s, 2s+1 = Im) of a
@@ -268,7 +268,10 @@ __device__ __forceinline__ long long next_digit(long long& x, int q) {
 template <bool ROWS_CONTIG>
 __global__ void oz_slice_kernel(OzSplit o) {
   __shared__ double2 tile[32][65];
+  __shared__ __nv_bfloat16 digit_bf16[2 * (1 << OZ_P) + 1];  // bf16 of the integers -2^P .. 2^P
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+  for (int t = threadIdx.y * 32 + threadIdx.x; t <= 2 * (1 << OZ_P); t += 256)
+    digit_bf16[t] = __float2bfloat16_rn((float)(t - (1 << OZ_P)));
   if (ROWS_CONTIG) {
     for (int kk = threadIdx.y; kk < 64; kk += 8) {
       const int r = r0 + threadIdx.x, k = k0 + kk;
@@ -297,16 +300,23 @@ __global__ void oz_slice_kernel(OzSplit o) {
     const bool fin = e != OZ_NONFINITE;
     // entries past K are zero (tile padding), so the pair never needs a tail case
     const double2 v0 = tile[i][2 * threadIdx.x], v1 = tile[i][2 * threadIdx.x + 1];
-    long long x0r = fin ? to_fixed(v0.x, e, F) : 0, x0i = fin ? to_fixed(v0.y, e, F) : 0;
-    long long x1r = fin ? to_fixed(v1.x, e, F) : 0, x1i = fin ? to_fixed(v1.y, e, F) : 0;
+    unsigned long long C = 0;
+    for (int s = 0; s < o.G; ++s) C += (1ull << OZ_P) << (OZ_W * (o.G - 1 - s));
+    const unsigned long long u0r = (unsigned long long)(fin ? to_fixed(v0.x, e, F) : 0) + C;
+    const unsigned long long u0i = (unsigned long long)(fin ? to_fixed(v0.y, e, F) : 0) + C;
+    const unsigned long long u1r = (unsigned long long)(fin ? to_fixed(v1.x, e, F) : 0) + C;
+    const unsigned long long u1i = (unsigned long long)(fin ? to_fixed(v1.y, e, F) : 0) + C;
     __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(o.dst + (long long)r * o.row_pitch + k);
     const long long ps2 = o.plane_stride / 2;  // plane stride in bf16 pairs (even: rows are padded to 8)
+    constexpr int H = 1 << OZ_P;
     for (int s = 0; s < o.G; ++s) {
-      const int q = OZ_W * (o.G - 1 - s);
-      const float d0r = (float)next_digit(x0r, q), d1r = (float)next_digit(x1r, q);
-      const float d0i = (float)next_digit(x0i, q), d1i = (float)next_digit(x1i, q);
-      dst[(long long)(2 * s) * ps2] = __floats2bfloat162_rn(d0r, d1r);
-      dst[(long long)(2 * s + 1) * ps2] = __floats2bfloat162_rn(d0i, d1i);
+      __nv_bfloat162 re, im;
+      re.x = digit_bf16[digit_of(u0r, s, o.G) + H];
+      re.y = digit_bf16[digit_of(u1r, s, o.G) + H];
+      im.x = digit_bf16[digit_of(u0i, s, o.G) + H];
+      im.y = digit_bf16[digit_of(u1i, s, o.G) + H];
+      dst[(long long)(2 * s) * ps2] = re;
+      dst[(long long)(2 * s + 1) * ps2] = im;
     }
   }
 }
