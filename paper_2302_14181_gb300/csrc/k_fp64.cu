@@ -307,10 +307,26 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
+// both parts in one round of barriers; each part is summed in block_sum's order
 __device__ double2 block_csum(double2 v, double* red) {
-  double a = block_sum(v.x, red);
-  double b = block_sum(v.y, red + 32);
-  return make_double2(a, b);
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    red[wid] = v.x;
+    red[32 + wid] = v.y;
+  }
+  __syncthreads();
+  double2 s = make_double2(0.0, 0.0);
+  const int nw = blockDim.x >> 5;
+  for (int w = 0; w < nw; ++w) {
+    s.x += red[w];
+    s.y += red[32 + w];
+  }
+  return s;
 }
 
 // sum |A|^2 of the m x n matrix (partial sums per block, fixed grid)
@@ -577,12 +593,64 @@ __device__ void apply_reflector(double2* col, const double2* v, double2 tau, int
   __syncthreads();
 }
 
+// the look-ahead step of the owner of column k1 = k + 1: apply reflector k to
+// that column and form reflector k1 from the result, with two block
+// reductions. Every sum runs over the rows in the order apply_reflector and
+// make_reflector use, so the result is bitwise that of those two calls.
+__device__ void apply_then_reflect(double2* col, const double2* v, double2 t, int k, int m, double tol,
+                                   double2* vout, double2* tau_out, double2* beta_out, double* red,
+                                   double2* s_alpha) {
+  const int k1 = k + 1;
+  const bool act = !(t.x == 0.0 && t.y == 0.0);  // uniform across the block
+  double2 f = make_double2(0.0, 0.0);
+  if (act) {
+    double2 w = make_double2(0.0, 0.0);
+    for (int r = k + threadIdx.x; r < m; r += blockDim.x) w = cfma(cconj(v[r]), col[r], w);
+    w = block_csum(w, red);
+    f = cmul(cconj(t), w);
+  }
+  if (act && threadIdx.x == 0) {  // row k: the R entry of the column
+    const double2 d = cmul(v[k], f);
+    col[k] = make_double2(col[k].x - d.x, col[k].y - d.y);
+  }
+  double s = 0.0;
+  for (int r = k1 + threadIdx.x; r < m; r += blockDim.x) {
+    double2 x = col[r];
+    if (act) {
+      const double2 d = cmul(v[r], f);
+      x = make_double2(x.x - d.x, x.y - d.y);
+      col[r] = x;
+    }
+    s = fma(x.x, x.x, s);
+    s = fma(x.y, x.y, s);
+    if (r == k1) *s_alpha = x;
+  }
+  const double nrm = sqrt(block_sum(s, red));  // its barriers also publish s_alpha
+  const double2 alpha = *s_alpha;
+  const bool deflate = (nrm <= tol) || (nrm == 0.0);
+  if (deflate) {
+    for (int r = k1 + threadIdx.x; r < m; r += blockDim.x) vout[r] = make_double2(r == k1 ? 1.0 : 0.0, 0.0);
+    *tau_out = make_double2(0.0, 0.0);
+    *beta_out = alpha;
+    return;
+  }
+  const double b = alpha.x >= 0.0 ? -nrm : nrm;
+  const double2 den = make_double2(alpha.x - b, alpha.y);
+  const double dd = den.x * den.x + den.y * den.y;
+  const double2 inv = make_double2(den.x / dd, -den.y / dd);
+  // each thread scales the rows it updated above
+  for (int r = k1 + threadIdx.x; r < m; r += blockDim.x)
+    vout[r] = (r == k1) ? make_double2(1.0, 0.0) : cmul(col[r], inv);
+  *tau_out = make_double2((b - alpha.x) / b, -alpha.y / b);
+  *beta_out = make_double2(b, 0.0);
+}
+
 __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, double2* V, double2* tau,
                                                       double2* beta, const double* frob2, int* flags, int epoch,
                                                       int* err) {
   extern __shared__ double2 sm[];
   __shared__ double red[64];
-  __shared__ double2 s_tau[2], s_beta;
+  __shared__ double2 s_tau[2], s_beta, s_alpha;
   __shared__ int s_abort;
   const int G = gridDim.x, c = blockIdx.x;
   const int ncols = (n - c + G - 1) / G;  // columns owned
@@ -653,9 +721,8 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
     const int k1 = k + 1;
     if (k1 < n && (k1 % G) == c) {
       double2* col = cols + (size_t)(k1 / G) * m;
-      apply_reflector(col, v, t, k, m, red);
       double2 t1, b1;
-      make_reflector(col, vb[k1 & 1], k1, m, tol, &t1, &b1, red);
+      apply_then_reflect(col, v, t, k, m, tol, vb[k1 & 1], &t1, &b1, red, &s_alpha);
       if (threadIdx.x == 0) {
         s_tau[k1 & 1] = t1;
         s_beta = b1;
