@@ -413,111 +413,25 @@ __global__ void qr_step_kernel(double2* A, int m, int n, int k, double2* V, doub
   }
 }
 
-// Q formation in blocks of QR_NB reflectors (compact WY form): the product
-// H_k0 ... H_k0+NB-1 equals I - V_b T_b V_b^H with V_b the block's reflector
-// columns and T_b upper triangular, built forward: T[i][i] = tau_i and
-// T[j][i] = -tau_i sum_{j <= l < i} T[j][l] (v_l^H v_i) for j < i. A column of Q
-// then needs one block reduction per block instead of one per reflector.
-constexpr int QR_NB = 4;
-
-__global__ void qr_block_t_kernel(const double2* V, const double2* tau, int m, int n, double2* T) {
-  __shared__ double red[64];
-  __shared__ double2 g[QR_NB][QR_NB];
-  const int k0 = blockIdx.x * QR_NB;
-  for (int a = 0; a < QR_NB; ++a)
-    for (int c = a + 1; c < QR_NB; ++c) {
-      double2 w = make_double2(0.0, 0.0);
-      if (k0 + c < n) {  // uniform across the block
-        const double2* va = V + (long long)(k0 + a) * m;
-        const double2* vc = V + (long long)(k0 + c) * m;
-        for (int r = k0 + c + threadIdx.x; r < m; r += blockDim.x) w = cfma(cconj(va[r]), vc[r], w);
-      }
-      w = block_csum(w, red);
-      if (threadIdx.x == 0) g[a][c] = w;
-    }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double2 t[QR_NB][QR_NB];
-    for (int i = 0; i < QR_NB; ++i)
-      for (int j = 0; j < QR_NB; ++j) t[i][j] = make_double2(0.0, 0.0);
-    for (int i = 0; i < QR_NB; ++i) {
-      const double2 ti = (k0 + i < n) ? tau[k0 + i] : make_double2(0.0, 0.0);
-      for (int j = 0; j < i; ++j) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int l = j; l < i; ++l) s = cfma(t[j][l], g[l][i], s);
-        const double2 v = cmul(ti, s);
-        t[j][i] = make_double2(-v.x, -v.y);
-      }
-      t[i][i] = ti;
-    }
-    for (int i = 0; i < QR_NB; ++i)
-      for (int j = 0; j < QR_NB; ++j) T[(long long)blockIdx.x * QR_NB * QR_NB + i * QR_NB + j] = t[i][j];
-  }
-}
-
-// sum of 2 QR_NB doubles over the block, the same fixed order in every thread
-__device__ void block_sum_nb(double* v, double* red) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < 2 * QR_NB; ++i)
-    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int i = 0; i < 2 * QR_NB; ++i) red[wid * 2 * QR_NB + i] = v[i];
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < 2 * QR_NB; ++i) {
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += red[w * 2 * QR_NB + i];
-    v[i] = s;
-  }
-}
-
-// column c of Q = H_0 ... H_c e_c, applied block by block from the last block
-// that reaches column c: q <- q - V_b (T_b (V_b^H q))
-__global__ void qr_form_q_blocked_kernel(const double2* V, const double2* T, int m, int n, double2* Q,
-                                         long long sQr, long long sQc) {
+// Q column c = H_0 H_1 ... H_c e_c, one CTA per column; q kept in shared memory
+__global__ void qr_form_q_kernel(const double2* V, const double2* tau, int m, int n, double2* Q,
+                                 long long sQr, long long sQc) {
   extern __shared__ double2 q[];
-  __shared__ double red[32 * 2 * QR_NB];
+  __shared__ double red[64];
   const int c = blockIdx.x;
   for (int r = threadIdx.x; r < m; r += blockDim.x) q[r] = make_double2(r == c ? 1.0 : 0.0, 0.0);
   __syncthreads();
-  for (int b = c / QR_NB; b >= 0; --b) {
-    const int k0 = b * QR_NB, nb = min(QR_NB, n - k0);
-    double s[2 * QR_NB];
-#pragma unroll
-    for (int i = 0; i < 2 * QR_NB; ++i) s[i] = 0.0;
-    for (int r = k0 + threadIdx.x; r < m; r += blockDim.x) {
-      const double2 x = q[r];
-#pragma unroll
-      for (int i = 0; i < QR_NB; ++i)
-        if (i < nb && r >= k0 + i) {
-          const double2 w = cfma(cconj(V[(long long)(k0 + i) * m + r]), x, make_double2(s[2 * i], s[2 * i + 1]));
-          s[2 * i] = w.x;
-          s[2 * i + 1] = w.y;
-        }
-    }
-    block_sum_nb(s, red);
-    const double2* Tb = T + (long long)b * QR_NB * QR_NB;
-    double2 y[QR_NB];
-#pragma unroll
-    for (int i = 0; i < QR_NB; ++i) {
-      double2 a = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int j = 0; j < QR_NB; ++j)
-        if (j >= i) a = cfma(Tb[i * QR_NB + j], make_double2(s[2 * j], s[2 * j + 1]), a);
-      y[i] = a;
-    }
-    for (int r = k0 + threadIdx.x; r < m; r += blockDim.x) {
-      double2 x = q[r];
-#pragma unroll
-      for (int i = 0; i < QR_NB; ++i)
-        if (i < nb && r >= k0 + i) {
-          const double2 d = cmul(V[(long long)(k0 + i) * m + r], y[i]);
-          x = make_double2(x.x - d.x, x.y - d.y);
-        }
-      q[r] = x;
+  for (int k = c; k >= 0; --k) {
+    const double2 t = tau[k];
+    if (t.x == 0.0 && t.y == 0.0) continue;  // uniform across the block
+    const double2* vk = V + (long long)k * m;
+    double2 w = make_double2(0.0, 0.0);
+    for (int r = k + threadIdx.x; r < m; r += blockDim.x) w = cfma(cconj(vk[r]), q[r], w);
+    w = block_csum(w, red);
+    const double2 f = cmul(t, w);
+    for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
+      double2 d = cmul(vk[r], f);
+      q[r] = make_double2(q[r].x - d.x, q[r].y - d.y);
     }
     __syncthreads();
   }
@@ -774,7 +688,7 @@ int qr64_factor(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_, z64*
     static bool attr_set = false;
     if (!attr_set) {
       cudaFuncSetAttribute(qr_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      cudaFuncSetAttribute(qr_form_q_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(qr_form_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       attr_set = true;
     }
   }
@@ -825,23 +739,17 @@ int qr64_factor_coop(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_,
 }
 
 int qr64_form_q(const Launch& L, const z64* V, const z64* tau, int m, int n, z64* Q, long long sQr,
-                long long sQc, z64* tblocks) {
+                long long sQc) {
   const size_t smem = sizeof(double2) * (size_t)m;
   const double fflops = 8.0 * (4.0 * (double)m * n * n - 4.0 / 3.0 * (double)n * n * n) / 2.0;
   int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_FORMQ, fflops, 32.0 * (double)m * n) : -1;
-  const int nblk = (n + QR_NB - 1) / QR_NB;
-  qr_block_t_kernel<<<nblk, QR_THREADS, 0, L.stream>>>(reinterpret_cast<const double2*>(V),
-                                                        reinterpret_cast<const double2*>(tau), m, n,
-                                                        reinterpret_cast<double2*>(tblocks));
-  qr_form_q_blocked_kernel<<<n, QR_THREADS, smem, L.stream>>>(reinterpret_cast<const double2*>(V),
-                                                              reinterpret_cast<const double2*>(tblocks), m, n,
-                                                              reinterpret_cast<double2*>(Q), sQr, sQc);
-  *L.launches += 2;
+  qr_form_q_kernel<<<n, QR_THREADS, smem, L.stream>>>(reinterpret_cast<const double2*>(V),
+                                                      reinterpret_cast<const double2*>(tau), m, n,
+                                                      reinterpret_cast<double2*>(Q), sQr, sQc);
+  ++*L.launches;
   if (L.prof) L.prof->end(L.stream, pr);
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
 }
-
-size_t qr64_form_q_scratch(int n) { return sizeof(z64) * (size_t)QR_NB * QR_NB * ((n + QR_NB - 1) / QR_NB); }
 
 int qr64_extract_r(const Launch& L, const z64* A, const z64* beta, int m, int n, z64* R) {
   long long total = (long long)n * n;

@@ -100,11 +100,9 @@ int qr64_factor(const Launch& L, z64* A, int m, int n, z64* V, z64* tau, z64* be
 // TEVO_EUNSUPPORTED when the matrix does not fit (then use qr64_factor)
 int qr64_factor_coop(const Launch& L, z64* A, int m, int n, z64* V, z64* tau, z64* beta, void* scratch, int* flags,
                      int epoch, int* err);
-// explicit thin Q (m x n) written with element (r, c) at Q[r * sQr + c * sQc];
-// tblocks: device scratch of qr64_form_q_scratch(n) bytes (block T factors)
+// explicit thin Q (m x n) written with element (r, c) at Q[r * sQr + c * sQc]
 int qr64_form_q(const Launch& L, const z64* V, const z64* tau, int m, int n, z64* Q, long long sQr,
-                long long sQc, z64* tblocks);
-size_t qr64_form_q_scratch(int n);
+                long long sQc);
 // R (n x n) from the factored A and beta: dense upper-triangular, row-major
 int qr64_extract_r(const Launch& L, const z64* A, const z64* beta, int m, int n, z64* R);
 
