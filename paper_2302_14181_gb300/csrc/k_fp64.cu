@@ -415,10 +415,13 @@ __global__ void qr_step_kernel(double2* A, int m, int n, int k, double2* V, doub
 
 // Q column c = H_0 H_1 ... H_c e_c, one CTA per column; q kept in shared memory
 __global__ void qr_form_q_kernel(const double2* V, const double2* tau, int m, int n, double2* Q,
-                                 long long sQr, long long sQc) {
+                                 long long sQr, long long sQc, int heavy) {
   extern __shared__ double2 q[];
   __shared__ double red[64];
-  const int c = blockIdx.x;
+  // column c costs c + 1 reflector applications: the first `heavy` blocks take
+  // the most expensive columns and the rest the cheapest ones, so that blocks
+  // sharing a multiprocessor pair a long column with a short one
+  const int c = (int)blockIdx.x < heavy ? n - 1 - (int)blockIdx.x : (int)blockIdx.x - heavy;
   for (int r = threadIdx.x; r < m; r += blockDim.x) q[r] = make_double2(r == c ? 1.0 : 0.0, 0.0);
   __syncthreads();
   for (int k = c; k >= 0; --k) {
@@ -591,7 +594,8 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
     if (threadIdx.x == 0) {
       tau[k] = s_tau[k & 1];
       beta[k] = s_beta;
-      __threadfence();
+      // the release store orders every write before it, including the other
+      // threads' stores that the block barrier above ordered before this thread
       st_release(flags + k, epoch);
     }
   };
@@ -745,7 +749,8 @@ int qr64_form_q(const Launch& L, const z64* V, const z64* tau, int m, int n, z64
   int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_FORMQ, fflops, 32.0 * (double)m * n) : -1;
   qr_form_q_kernel<<<n, QR_THREADS, smem, L.stream>>>(reinterpret_cast<const double2*>(V),
                                                       reinterpret_cast<const double2*>(tau), m, n,
-                                                      reinterpret_cast<double2*>(Q), sQr, sQc);
+                                                      reinterpret_cast<double2*>(Q), sQr, sQc,
+                                                      std::min(n, L.num_sms));
   ++*L.launches;
   if (L.prof) L.prof->end(L.stream, pr);
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
