@@ -293,6 +293,10 @@ int zsparse_g2(const Launch& L, const z64* X, z64* T, const int* row_ptr, const 
 namespace {
 
 constexpr int QR_THREADS = 128;
+// upper bound on the CTAs of the cooperative factorisation (compile-time choice)
+#ifndef QR_COOP_MAX_CTAS
+#define QR_COOP_MAX_CTAS 1024
+#endif
 constexpr double DEFLATE = 2.2737367544323206e-13;  // 2^-42
 
 __device__ double block_sum(double v, double* red) {
@@ -712,7 +716,7 @@ int qr64_factor_coop(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_,
   double2* A = reinterpret_cast<double2*>(A_);
   double* part = reinterpret_cast<double*>(scratch);
   double* frob2 = part + FROB_BLOCKS;
-  const int G = std::min(n, L.num_sms);
+  const int G = std::min({n, L.num_sms, QR_COOP_MAX_CTAS});
   const int ncols = (n + G - 1) / G;
   const size_t smem = sizeof(double2) * (size_t)(ncols + 2) * m;
   if (smem > 200 * 1024) return TEVO_EUNSUPPORTED;
