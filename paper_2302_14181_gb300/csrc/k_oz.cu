@@ -18,7 +18,7 @@
 //
 // C is formed from the slice pairs (s, t) with s + t < G, grouped by g = s + t
 // (all pairs of a group carry the weight 2^-(2P + W g)). One pass accumulates a
-// group over a chunk of at most 256 K-indices: 2 (g + 1) * 256 <= 4096 terms, so
+// group over at most 2048 / (g + 1) K-indices: 2 (g + 1) K <= 4096 terms, so
 // the pass result is exact. The epilogue turns it into an integer and adds it,
 // shifted by its group's weight, to a 64-bit fixed-point sum per output entry;
 // after the last pass of a tile the sum is scaled by 2^(e_m + e_n) and rounded
@@ -429,10 +429,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     c1 = min(a.nchunks, c0 + a.cps);
     return z;
   };
-  auto chunk_tiles = [&](int c, int& kt0, int& kt1) {
-    kt0 = c * OZ_KT_CHUNK;
-    kt1 = min(a.k_tiles, kt0 + OZ_KT_CHUNK);
+  // a unit covers the K-tiles [c0 * OZ_KT_CHUNK, min(c1 * OZ_KT_CHUNK, k_tiles));
+  // a pass of group g spans at most 64 / (g + 1) K-tiles of 32, the longest
+  // for which its 2 (g + 1) K products per entry stay exact in fp32 (so the
+  // low groups, with little MMA work per K, need fewer passes)
+  auto unit_tiles = [&](int c0, int c1, int& t0, int& t1) {
+    t0 = c0 * OZ_KT_CHUNK;
+    t1 = min(a.k_tiles, c1 * OZ_KT_CHUNK);
   };
+  auto pass_len = [&](int g) { return (2048 / 32) / (g + 1); };
 
   if (warp == 0) {
     if (lane == 0) {
@@ -444,11 +449,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int u = cid; u < nunits && ok; u += ncl) {
         int m0, n0, c0, c1;
         unit_of(u, m0, n0, c0, c1);
-        for (int c = c0; c < c1 && ok; ++c) {
-          int kt0, kt1;
-          chunk_tiles(c, kt0, kt1);
-          for (int g = 0; g < a.G && ok; ++g)
-            for (int kt = kt0; kt < kt1 && ok; ++kt)
+        int t0, t1;
+        unit_tiles(c0, c1, t0, t1);
+        for (int g = 0; g < a.G && ok; ++g)
+          for (int p0 = t0; p0 < t1 && ok; p0 += pass_len(g))
+            for (int kt = p0; kt < min(t1, p0 + pass_len(g)) && ok; ++kt)
               for (int s = 0; s <= g; ++s, ++q) {
                 const int st = int(q % OZ_NSTAGE);
                 if (!mbar_wait(empty0 + 8 * st, (uint32_t(q / OZ_NSTAGE) & 1u) ^ 1u, a.err, 1)) {
@@ -469,7 +474,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                   tma_load_4d_mc(hb + OZ_TN * OZ_KCB, &tmBh, kt * 32, 0, nh, 2 * (g - s) + 1, fb, (uint16_t)0x3);
                 }
               }
-        }
       }
       // do not leave while copies are in flight
       for (long long r = (q > OZ_NSTAGE ? q - OZ_NSTAGE : 0); r < q; ++r)
@@ -488,10 +492,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int u = cid; u < nunits && ok; u += ncl) {
         int m0, n0, c0, c1;
         unit_of(u, m0, n0, c0, c1);
-        for (int c = c0; c < c1 && ok; ++c) {
-          int kt0, kt1;
-          chunk_tiles(c, kt0, kt1);
-          for (int g = 0; g < a.G && ok; ++g, ++i) {
+        int t0, t1;
+        unit_tiles(c0, c1, t0, t1);
+        for (int g = 0; g < a.G && ok; ++g)
+          for (int p0 = t0; p0 < t1 && ok; p0 += pass_len(g), ++i) {
+            const int kt0 = p0, kt1 = min(t1, p0 + pass_len(g));
             const int b = i & 1;
             if (!mbar_wait(tempty0 + 8 * b, (uint32_t(i >> 1) & 1u) ^ 1u, a.err, 5)) {
               ok = false;
@@ -527,7 +532,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               }
             mma_commit(tfull0 + 8 * b);
           }
-        }
       }
     }
   } else {
@@ -550,15 +554,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const int z = unit_of(u, m0, n0, c0, c1);
       const int m = m0 + row;
       const int em = m < a.M ? a.ea[m] : 0;
-      for (int c = c0; c < c1 && ok; ++c)
-        for (int g = 0; g < a.G; ++g, ++i) {
+      int t0, t1;
+      unit_tiles(c0, c1, t0, t1);
+      for (int g = 0; g < a.G && ok; ++g)
+        for (int p0 = t0; p0 < t1; p0 += pass_len(g), ++i) {
           const int b = i & 1;
           if (!mbar_wait(tfull0 + 8 * b, uint32_t(i >> 1) & 1u, a.err, 4)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const bool first = (c == c0 && g == 0), last = (c == c1 - 1 && g == a.G - 1);
+          const bool first = (g == 0 && p0 == t0), last = (g == a.G - 1 && p0 + pass_len(g) >= t1);
           // weight of this group in S: 2^(base_shift - W g) units of the pass value
           const int shift = a.base_shift - OZ_W * g;
           const uint32_t trow = tmem + (uint32_t)(b * 2 * OZ_TN) + ((uint32_t)(qw * 32) << 16);
