@@ -60,7 +60,7 @@ extern "C" {
  * digit slices of 7 bits, digit products are exact and their sums are exact in
  * the fp32 accumulator, and the pass results are scaled and summed in fp64.
  * With G slices the dropped part is about (G + 2) 2^(-7 G) of
- * max|row of A| max|row of B| K per entry (G = 7: 49 bits; a native fp64 GEMM
+ * max|row of A| max|row of B| K per entry (G = 8: 56 bits; a native fp64 GEMM
  * has about K 2^-53 of sum |A||B|). Inputs, outputs, the QR, the norm and the
  * reductions stay fp64. TEVO_OZAKI_SLICES(G) picks G in 1..8 (default 8: 56 bits).
  * Not in the paper: a GB300-specific way to run the fp64 sweep, whose fp64

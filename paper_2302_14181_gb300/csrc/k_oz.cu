@@ -24,7 +24,7 @@
 // after the last pass of a tile the sum is scaled by 2^(e_m + e_n) and rounded
 // once to fp64. The only errors are the dropped terms (digits past slice G-1
 // and pairs with s + t >= G), relative size about (G + 2) 2^-(W G) of
-// max|A_m.| max|B_n.| K (G = 7: 49 bits), the few bits of the last groups
+// max|A_m.| max|B_n.| K (G = 8: 56 bits), the few bits of the last groups
 // below the fixed-point unit, and that final rounding. No per-pass work uses
 // the fp64 pipe, which on this part runs at about 1/1600 of the bf16 MMA rate.
 //
