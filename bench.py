@@ -474,12 +474,12 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("TEVO_BENCH_PRECISION", "tf32x3+oz"), choices=sorted(PREC))
+    ap.add_argument("--precision", default=os.environ.get("TEVO_BENCH_PRECISION", "bf16x3+oz"), choices=sorted(PREC))
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the fp64-form step timed beside the mixed form")
     ap.add_argument("--sweeps", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--verify", action="store_true", help="run the t = 5 evolution in each form against the oracle")
-    ap.add_argument("--verify-forms", default="tf32x3+oz,bf16x3+oz,fp64+oz,bf16x3,fp64")
+    ap.add_argument("--verify-forms", default="bf16x3+oz,tf32x3+oz,fp64+oz,bf16x3,fp64")
     args = ap.parse_args()
     if args.verify:
         verify(args)
