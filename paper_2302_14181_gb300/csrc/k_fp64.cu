@@ -297,10 +297,6 @@ constexpr int QR_THREADS = 128;
 #ifndef QR_COOP_MAX_CTAS
 #define QR_COOP_MAX_CTAS 1024
 #endif
-// consecutive columns per owner block in the cooperative factorisation
-#ifndef QR_OWN_BLOCK
-#define QR_OWN_BLOCK 2
-#endif
 constexpr double DEFLATE = 2.2737367544323206e-13;  // 2^-42
 
 __device__ double block_sum(double v, double* red) {
@@ -449,15 +445,13 @@ __global__ void qr_form_q_kernel(const double2* V, const double2* tau, int m, in
   for (int r = threadIdx.x; r < m; r += blockDim.x) Q[(long long)r * sQr + (long long)c * sQc] = q[r];
 }
 
-// Cooperative Householder factorisation, one launch for all columns. The columns
-// are dealt to the CTAs in blocks of QR_OWN_BLOCK (block b to CTA b mod G, G =
-// grid size) and kept in shared memory. At
+// Cooperative Householder factorisation, one launch for all columns. CTA c owns
+// columns j = c, c + G, c + 2G, ... (G = grid size), kept in shared memory. At
 // step k the owner of column k publishes reflector k (V[:, k], tau[k], beta[k],
 // then a release flag), every other CTA acquires it and applies H_k^H to its own
 // columns > k. The owner of column k + 1 updates that column first and publishes
 // reflector k + 1 before updating its other columns, so the chain of dependent
-// work per step is one column update plus one norm; inside a block the owner
-// goes on from its own reflector without waiting for a hand-off. All CTAs are co-resident
+// work per step is one column update plus one norm. All CTAs are co-resident
 // (cooperative launch); every wait is bounded (err, code 8) and, after a
 // timeout, all CTAs leave.
 constexpr unsigned long long QR_WAIT_NS = 2000000000ull;
@@ -580,20 +574,12 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
   __shared__ double2 s_tau[2], s_beta, s_alpha;
   __shared__ int s_abort;
   const int G = gridDim.x, c = blockIdx.x;
-  // block-cyclic ownership: blocks of QR_OWN_BLOCK consecutive columns go to the
-  // CTAs in turn, so a CTA forms the reflectors of its block one after another
-  // without a hand-off through global memory in between
-  const int nblk = (n + QR_OWN_BLOCK - 1) / QR_OWN_BLOCK;
-  const int ncols = ((nblk + G - 1) / G) * QR_OWN_BLOCK;  // local column slots (some past n)
-  auto gcol = [&](int jj) { return ((jj / QR_OWN_BLOCK) * G + c) * QR_OWN_BLOCK + jj % QR_OWN_BLOCK; };
-  auto owner_of = [&](int j) { return (j / QR_OWN_BLOCK) % G; };
-  auto lidx = [&](int j) { return ((j / QR_OWN_BLOCK) / G) * QR_OWN_BLOCK + j % QR_OWN_BLOCK; };
+  const int ncols = (n - c + G - 1) / G;  // columns owned
   double2* cols = sm;                      // [ncols][m]
   double2* vb[2] = {sm + (size_t)ncols * m, sm + (size_t)(ncols + 1) * m};
   const double tol = DEFLATE * sqrt(*frob2);
   for (int jj = 0; jj < ncols; ++jj) {
-    const int j = gcol(jj);
-    if (j >= n) continue;
+    const int j = c + jj * G;
     for (int r = threadIdx.x; r < m; r += blockDim.x) cols[(size_t)jj * m + r] = A[(long long)j * m + r];
   }
   if (threadIdx.x == 0) s_abort = 0;
@@ -604,7 +590,7 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
     double2* Vk = V + (long long)k * m;
     for (int r = threadIdx.x; r < m; r += blockDim.x) Vk[r] = (r < k) ? make_double2(0.0, 0.0) : v[r];
     // the R part of column k (rows above k) for qr64_extract_r
-    const double2* col = cols + (size_t)lidx(k) * m;
+    const double2* col = cols + (size_t)(k / G) * m;
     for (int r = threadIdx.x; r < k; r += blockDim.x) A[(long long)k * m + r] = col[r];
     // the block barrier orders every thread's stores before thread 0's device
     // fence and release below (one fence per block, not one per thread)
@@ -629,7 +615,7 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
     publish(0);
   }
   for (int k = 0; k < n; ++k) {
-    const int owner = owner_of(k);
+    const int owner = k % G;
     double2* v = vb[k & 1];
     if (owner != c) {
       // acquire reflector k
@@ -655,8 +641,8 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
     const double2 t = s_tau[k & 1];
     // look-ahead: column k + 1 first, then publish reflector k + 1
     const int k1 = k + 1;
-    if (k1 < n && owner_of(k1) == c) {
-      double2* col = cols + (size_t)lidx(k1) * m;
+    if (k1 < n && (k1 % G) == c) {
+      double2* col = cols + (size_t)(k1 / G) * m;
       double2 t1, b1;
       apply_then_reflect(col, v, t, k, m, tol, vb[k1 & 1], &t1, &b1, red, &s_alpha);
       if (threadIdx.x == 0) {
@@ -667,8 +653,8 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
       publish(k1);
     }
     for (int jj = 0; jj < ncols; ++jj) {
-      const int j = gcol(jj);
-      if (j >= n || j <= k || j == k1) continue;
+      const int j = c + jj * G;
+      if (j <= k || j == k1) continue;
       apply_reflector(cols + (size_t)jj * m, v, t, k, m, red);
     }
   }
@@ -730,9 +716,8 @@ int qr64_factor_coop(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_,
   double2* A = reinterpret_cast<double2*>(A_);
   double* part = reinterpret_cast<double*>(scratch);
   double* frob2 = part + FROB_BLOCKS;
-  const int nblk = (n + QR_OWN_BLOCK - 1) / QR_OWN_BLOCK;
-  const int G = std::min({nblk, L.num_sms, QR_COOP_MAX_CTAS});
-  const int ncols = ((nblk + G - 1) / G) * QR_OWN_BLOCK;
+  const int G = std::min({n, L.num_sms, QR_COOP_MAX_CTAS});
+  const int ncols = (n + G - 1) / G;
   const size_t smem = sizeof(double2) * (size_t)(ncols + 2) * m;
   if (smem > 200 * 1024) return TEVO_EUNSUPPORTED;
   static bool attr = false;
