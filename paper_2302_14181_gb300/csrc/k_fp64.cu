@@ -299,38 +299,78 @@ constexpr int QR_THREADS = 128;
 #endif
 constexpr double DEFLATE = 2.2737367544323206e-13;  // 2^-42
 
-__device__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// Block reductions. Lane 0 of each warp ends with the warp's sum; at offset o
+// only lanes below o feed a lane that a later offset reads, so the others skip
+// the add (lane 0's sum is that of the full tree). Thread 0 adds the warps'
+// sums in a fixed order and shares the total through shared memory: the
+// scalar fp64 work runs once per block, not once per thread. Blocks of at most
+// 512 threads (red[16] and red[48] hold the shared totals).
+__device__ __forceinline__ double warp_sum0(double v) {
+  const int lane = threadIdx.x & 31;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double u = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane < o) v += u;
+  }
+  return v;
+}
+
+__device__ __forceinline__ double2 warp_csum0(double2 v) {
+  const int lane = threadIdx.x & 31;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ux = __shfl_down_sync(0xffffffffu, v.x, o);
+    const double uy = __shfl_down_sync(0xffffffffu, v.y, o);
+    if (lane < o) {
+      v.x += ux;
+      v.y += uy;
+    }
+  }
+  return v;
+}
+
+// the warps' sums of v into red[0..nw) (thread 0 reads them after the barrier)
+__device__ __forceinline__ void block_partials(double v, double* red) {
+  v = warp_sum0(v);
   __syncthreads();
-  if (lane == 0) red[wid] = v;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
+}
+
+__device__ __forceinline__ double total_of(const double* red) {
   double s = 0.0;
   const int nw = blockDim.x >> 5;
-  for (int w = 0; w < nw; ++w) s += red[w];  // fixed order: identical in every thread
+  for (int w = 0; w < nw; ++w) s += red[w];  // fixed order
   return s;
 }
 
-// both parts in one round of barriers; each part is summed in block_sum's order
+__device__ double block_sum(double v, double* red) {
+  block_partials(v, red);
+  if (threadIdx.x == 0) red[16] = total_of(red);
+  __syncthreads();
+  return red[16];
+}
+
+// a * (the block's sum of v), for every thread; a = 1 gives the plain sum
+// (both parts summed in block_sum's order, one round of barriers)
+__device__ double2 block_csum_times(double2 v, double2 a, double* red, bool scale) {
+  v = warp_csum0(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = v.x;
+    red[32 + (threadIdx.x >> 5)] = v.y;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s = make_double2(total_of(red), total_of(red + 32));
+    if (scale) s = cmul(a, s);
+    red[16] = s.x;
+    red[48] = s.y;
+  }
+  __syncthreads();
+  return make_double2(red[16], red[48]);
+}
+
 __device__ double2 block_csum(double2 v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) {
-    red[wid] = v.x;
-    red[32 + wid] = v.y;
-  }
-  __syncthreads();
-  double2 s = make_double2(0.0, 0.0);
-  const int nw = blockDim.x >> 5;
-  for (int w = 0; w < nw; ++w) {
-    s.x += red[w];
-    s.y += red[32 + w];
-  }
-  return s;
+  return block_csum_times(v, make_double2(1.0, 0.0), red, false);
 }
 
 // sum |A|^2 of the m x n matrix (partial sums per block, fixed grid)
@@ -407,9 +447,8 @@ __global__ void qr_step_kernel(double2* A, int m, int n, int k, double2* V, doub
   // w = v^H col
   double2 w = make_double2(0.0, 0.0);
   for (int r = threadIdx.x; r < len; r += blockDim.x) w = cfma(cconj(v[r]), col[r], w);
-  w = block_csum(w, red);
   // col -= conj(t) v w
-  const double2 f = cmul(cconj(t), w);
+  const double2 f = block_csum_times(w, cconj(t), red, true);
   for (int r = threadIdx.x; r < len; r += blockDim.x) {
     double2 c = col[r];
     double2 d = cmul(v[r], f);
@@ -434,8 +473,7 @@ __global__ void qr_form_q_kernel(const double2* V, const double2* tau, int m, in
     const double2* vk = V + (long long)k * m;
     double2 w = make_double2(0.0, 0.0);
     for (int r = k + threadIdx.x; r < m; r += blockDim.x) w = cfma(cconj(vk[r]), q[r], w);
-    w = block_csum(w, red);
-    const double2 f = cmul(t, w);
+    const double2 f = block_csum_times(w, t, red, true);
     for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
       double2 d = cmul(vk[r], f);
       q[r] = make_double2(q[r].x - d.x, q[r].y - d.y);
@@ -445,15 +483,128 @@ __global__ void qr_form_q_kernel(const double2* V, const double2* tau, int m, in
   for (int r = threadIdx.x; r < m; r += blockDim.x) Q[(long long)r * sQr + (long long)c * sQc] = q[r];
 }
 
+// Householder scalars of a column (shared by every thread of the block)
+struct Refl {
+  double2 inv;   // 1 / (alpha - beta), the scale of the column below its first row
+  double2 tau;
+  double2 beta;
+  int deflate;
+};
+
+// The block's total of the per-thread squares s and the reflector of a column
+// whose first entry is alpha (read in thread 0 only). Thread 0 forms the
+// scalars once (deflation as in qr_step_kernel) and the block reads them.
+__device__ Refl block_reflector(double s, double2 alpha, double tol, double* red, Refl* sr) {
+  block_partials(s, red);
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(total_of(red));
+    Refl R;
+    R.deflate = (nrm <= tol) || (nrm == 0.0);
+    if (R.deflate) {
+      R.inv = make_double2(0.0, 0.0);
+      R.tau = make_double2(0.0, 0.0);
+      R.beta = alpha;
+    } else {
+      const double b = alpha.x >= 0.0 ? -nrm : nrm;
+      const double2 den = make_double2(alpha.x - b, alpha.y);
+      const double dd = den.x * den.x + den.y * den.y;
+      R.inv = make_double2(den.x / dd, -den.y / dd);
+      R.tau = make_double2((b - alpha.x) / b, -alpha.y / b);
+      R.beta = make_double2(b, 0.0);
+    }
+    *sr = R;
+  }
+  __syncthreads();
+  return *sr;
+}
+
+// reflector of the column x[k..m) (in shared memory) into vout[k..m) and the
+// global copy vg[k..m)
+__device__ Refl make_reflector(const double2* x, double2* vout, double2* vg, int k, int m, double tol,
+                               double* red, Refl* sr) {
+  double s = 0.0;
+  for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
+    double2 a = x[r];
+    s = fma(a.x, a.x, s);
+    s = fma(a.y, a.y, s);
+  }
+  const Refl R = block_reflector(s, x[k], tol, red, sr);
+  for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
+    const double2 e = R.deflate ? make_double2(r == k ? 1.0 : 0.0, 0.0)
+                                : ((r == k) ? make_double2(1.0, 0.0) : cmul(x[r], R.inv));
+    vout[r] = e;
+    vg[r] = e;
+  }
+  return R;
+}
+
+// col[k..m) -= conj(tau) v (v^H col[k..m))
+__device__ void apply_reflector(double2* col, const double2* v, double2 tau, int k, int m, double* red) {
+  if (tau.x == 0.0 && tau.y == 0.0) return;  // uniform across the block
+  double2 w = make_double2(0.0, 0.0);
+  for (int r = k + threadIdx.x; r < m; r += blockDim.x) w = cfma(cconj(v[r]), col[r], w);
+  const double2 f = block_csum_times(w, cconj(tau), red, true);
+  for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
+    double2 d = cmul(v[r], f);
+    col[r] = make_double2(col[r].x - d.x, col[r].y - d.y);
+  }
+  __syncthreads();
+}
+
+// the look-ahead step of the owner of column k1 = k + 1: apply reflector k to
+// that column and form reflector k1 from the result (into vout and its global
+// copy vg), with two block reductions. Every sum runs over the rows in the
+// order apply_reflector and make_reflector use, so the result is bitwise that
+// of those two calls. Thread 0 updates row k and holds row k1 (alpha).
+__device__ Refl apply_then_reflect(double2* col, const double2* v, double2 t, int k, int m, double tol,
+                                   double2* vout, double2* vg, double* red, Refl* sr) {
+  const int k1 = k + 1;
+  const bool act = !(t.x == 0.0 && t.y == 0.0);  // uniform across the block
+  double2 f = make_double2(0.0, 0.0);
+  if (act) {
+    double2 w = make_double2(0.0, 0.0);
+    for (int r = k + threadIdx.x; r < m; r += blockDim.x) w = cfma(cconj(v[r]), col[r], w);
+    f = block_csum_times(w, cconj(t), red, true);
+  }
+  if (act && threadIdx.x == 0) {  // row k: the R entry of the column
+    const double2 d = cmul(v[k], f);
+    col[k] = make_double2(col[k].x - d.x, col[k].y - d.y);
+  }
+  double s = 0.0;
+  double2 alpha = make_double2(0.0, 0.0);
+  for (int r = k1 + threadIdx.x; r < m; r += blockDim.x) {
+    double2 x = col[r];
+    if (act) {
+      const double2 d = cmul(v[r], f);
+      x = make_double2(x.x - d.x, x.y - d.y);
+      col[r] = x;
+    }
+    s = fma(x.x, x.x, s);
+    s = fma(x.y, x.y, s);
+    if (r == k1) alpha = x;
+  }
+  const Refl R = block_reflector(s, alpha, tol, red, sr);
+  // each thread scales the rows it updated above
+  for (int r = k1 + threadIdx.x; r < m; r += blockDim.x) {
+    const double2 e = R.deflate ? make_double2(r == k1 ? 1.0 : 0.0, 0.0)
+                                : ((r == k1) ? make_double2(1.0, 0.0) : cmul(col[r], R.inv));
+    vout[r] = e;
+    vg[r] = e;
+  }
+  return R;
+}
+
 // Cooperative Householder factorisation, one launch for all columns. CTA c owns
 // columns j = c, c + G, c + 2G, ... (G = grid size), kept in shared memory. At
-// step k the owner of column k publishes reflector k (V[:, k], tau[k], beta[k],
-// then a release flag), every other CTA acquires it and applies H_k^H to its own
-// columns > k. The owner of column k + 1 updates that column first and publishes
-// reflector k + 1 before updating its other columns, so the chain of dependent
-// work per step is one column update plus one norm. All CTAs are co-resident
-// (cooperative launch); every wait is bounded (err, code 8) and, after a
-// timeout, all CTAs leave.
+// step k the owner of column k publishes reflector k (V[k.., k], tau[k],
+// beta[k], then a release flag), every other CTA acquires it and applies H_k^H
+// to its own columns > k. The owner of column k + 1 updates that column first
+// and publishes reflector k + 1 before updating its other columns, so the chain
+// of dependent work per step is one column update plus one norm; the rows of
+// V above the diagonal and the R part of the column, which only later kernels
+// read, are written after the release. All CTAs are co-resident (cooperative
+// launch); every wait is bounded (err, code 8) and, after a timeout, all CTAs
+// leave.
 constexpr unsigned long long QR_WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ unsigned long long qr_gtimer() {
@@ -472,106 +623,13 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// reflector of the column x[k..m) (in shared memory) into vout[k..m); returns
-// tau, writes beta; deflation as in qr_step_kernel
-__device__ void make_reflector(const double2* x, double2* vout, int k, int m, double tol, double2* tau_out,
-                               double2* beta_out, double* red) {
-  double s = 0.0;
-  for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
-    double2 a = x[r];
-    s = fma(a.x, a.x, s);
-    s = fma(a.y, a.y, s);
-  }
-  const double nrm = sqrt(block_sum(s, red));
-  const double2 alpha = x[k];
-  const bool deflate = (nrm <= tol) || (nrm == 0.0);
-  if (deflate) {
-    for (int r = k + threadIdx.x; r < m; r += blockDim.x) vout[r] = make_double2(r == k ? 1.0 : 0.0, 0.0);
-    *tau_out = make_double2(0.0, 0.0);
-    *beta_out = alpha;
-    return;
-  }
-  const double b = alpha.x >= 0.0 ? -nrm : nrm;
-  const double2 den = make_double2(alpha.x - b, alpha.y);
-  const double dd = den.x * den.x + den.y * den.y;
-  const double2 inv = make_double2(den.x / dd, -den.y / dd);
-  for (int r = k + threadIdx.x; r < m; r += blockDim.x) vout[r] = (r == k) ? make_double2(1.0, 0.0) : cmul(x[r], inv);
-  *tau_out = make_double2((b - alpha.x) / b, -alpha.y / b);
-  *beta_out = make_double2(b, 0.0);
-}
-
-// col[k..m) -= conj(tau) v (v^H col[k..m))
-__device__ void apply_reflector(double2* col, const double2* v, double2 tau, int k, int m, double* red) {
-  if (tau.x == 0.0 && tau.y == 0.0) return;  // uniform across the block
-  double2 w = make_double2(0.0, 0.0);
-  for (int r = k + threadIdx.x; r < m; r += blockDim.x) w = cfma(cconj(v[r]), col[r], w);
-  w = block_csum(w, red);
-  const double2 f = cmul(cconj(tau), w);
-  for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
-    double2 d = cmul(v[r], f);
-    col[r] = make_double2(col[r].x - d.x, col[r].y - d.y);
-  }
-  __syncthreads();
-}
-
-// the look-ahead step of the owner of column k1 = k + 1: apply reflector k to
-// that column and form reflector k1 from the result, with two block
-// reductions. Every sum runs over the rows in the order apply_reflector and
-// make_reflector use, so the result is bitwise that of those two calls.
-__device__ void apply_then_reflect(double2* col, const double2* v, double2 t, int k, int m, double tol,
-                                   double2* vout, double2* tau_out, double2* beta_out, double* red,
-                                   double2* s_alpha) {
-  const int k1 = k + 1;
-  const bool act = !(t.x == 0.0 && t.y == 0.0);  // uniform across the block
-  double2 f = make_double2(0.0, 0.0);
-  if (act) {
-    double2 w = make_double2(0.0, 0.0);
-    for (int r = k + threadIdx.x; r < m; r += blockDim.x) w = cfma(cconj(v[r]), col[r], w);
-    w = block_csum(w, red);
-    f = cmul(cconj(t), w);
-  }
-  if (act && threadIdx.x == 0) {  // row k: the R entry of the column
-    const double2 d = cmul(v[k], f);
-    col[k] = make_double2(col[k].x - d.x, col[k].y - d.y);
-  }
-  double s = 0.0;
-  for (int r = k1 + threadIdx.x; r < m; r += blockDim.x) {
-    double2 x = col[r];
-    if (act) {
-      const double2 d = cmul(v[r], f);
-      x = make_double2(x.x - d.x, x.y - d.y);
-      col[r] = x;
-    }
-    s = fma(x.x, x.x, s);
-    s = fma(x.y, x.y, s);
-    if (r == k1) *s_alpha = x;
-  }
-  const double nrm = sqrt(block_sum(s, red));  // its barriers also publish s_alpha
-  const double2 alpha = *s_alpha;
-  const bool deflate = (nrm <= tol) || (nrm == 0.0);
-  if (deflate) {
-    for (int r = k1 + threadIdx.x; r < m; r += blockDim.x) vout[r] = make_double2(r == k1 ? 1.0 : 0.0, 0.0);
-    *tau_out = make_double2(0.0, 0.0);
-    *beta_out = alpha;
-    return;
-  }
-  const double b = alpha.x >= 0.0 ? -nrm : nrm;
-  const double2 den = make_double2(alpha.x - b, alpha.y);
-  const double dd = den.x * den.x + den.y * den.y;
-  const double2 inv = make_double2(den.x / dd, -den.y / dd);
-  // each thread scales the rows it updated above
-  for (int r = k1 + threadIdx.x; r < m; r += blockDim.x)
-    vout[r] = (r == k1) ? make_double2(1.0, 0.0) : cmul(col[r], inv);
-  *tau_out = make_double2((b - alpha.x) / b, -alpha.y / b);
-  *beta_out = make_double2(b, 0.0);
-}
-
 __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, double2* V, double2* tau,
                                                       double2* beta, const double* frob2, int* flags, int epoch,
                                                       int* err) {
   extern __shared__ double2 sm[];
   __shared__ double red[64];
-  __shared__ double2 s_tau[2], s_beta, s_alpha;
+  __shared__ double2 s_tau[2];
+  __shared__ Refl s_refl;
   __shared__ int s_abort;
   const int G = gridDim.x, c = blockIdx.x;
   const int ncols = (n - c + G - 1) / G;  // columns owned
@@ -584,35 +642,30 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
   }
   if (threadIdx.x == 0) s_abort = 0;
   __syncthreads();
-  // publish reflector k held in vb[k & 1] (called by the owner of column k)
-  auto publish = [&](int k) {
-    const double2* v = vb[k & 1];
-    double2* Vk = V + (long long)k * m;
-    for (int r = threadIdx.x; r < m; r += blockDim.x) Vk[r] = (r < k) ? make_double2(0.0, 0.0) : v[r];
-    // the R part of column k (rows above k) for qr64_extract_r
-    const double2* col = cols + (size_t)(k / G) * m;
-    for (int r = threadIdx.x; r < k; r += blockDim.x) A[(long long)k * m + r] = col[r];
-    // the block barrier orders every thread's stores before thread 0's device
-    // fence and release below (one fence per block, not one per thread)
-    __syncthreads();
+  // release reflector k, whose rows k.. of V are already stored by the threads
+  // that formed them (called by the owner of column k with s_refl holding its
+  // scalars)
+  auto release = [&](int k) {
     if (threadIdx.x == 0) {
-      tau[k] = s_tau[k & 1];
-      beta[k] = s_beta;
-      // the release store orders every write before it, including the other
-      // threads' stores that the block barrier above ordered before this thread
-      st_release(flags + k, epoch);
+      s_tau[k & 1] = s_refl.tau;
+      tau[k] = s_refl.tau;
+      beta[k] = s_refl.beta;
+    }
+    // the block barrier orders every thread's stores of V before thread 0's
+    // release store, which is cumulative over them (one release per block)
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(flags + k, epoch);
+    // rows above k: zeros of V, and the R part of column k for qr64_extract_r
+    const double2* col = cols + (size_t)(k / G) * m;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+      V[(long long)k * m + r] = make_double2(0.0, 0.0);
+      A[(long long)k * m + r] = col[r];
     }
   };
   // the owner of column 0 starts the chain
   if (c == 0) {
-    double2 t, b;
-    make_reflector(cols, vb[0], 0, m, tol, &t, &b, red);
-    if (threadIdx.x == 0) {
-      s_tau[0] = t;
-      s_beta = b;
-    }
-    __syncthreads();
-    publish(0);
+    make_reflector(cols, vb[0], V, 0, m, tol, red, &s_refl);
+    release(0);
   }
   for (int k = 0; k < n; ++k) {
     const int owner = k % G;
@@ -634,23 +687,19 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
       }
       __syncthreads();
       if (s_abort) return;
+      // each thread loads the rows it reads first (its own rows of the dot
+      // products below); other threads read them only after a reduction's
+      // barrier
       const double2* Vk = V + (long long)k * m;
       for (int r = k + threadIdx.x; r < m; r += blockDim.x) v[r] = __ldcg(Vk + r);  // L2, never a stale L1 line
-      __syncthreads();
     }
     const double2 t = s_tau[k & 1];
     // look-ahead: column k + 1 first, then publish reflector k + 1
     const int k1 = k + 1;
     if (k1 < n && (k1 % G) == c) {
       double2* col = cols + (size_t)(k1 / G) * m;
-      double2 t1, b1;
-      apply_then_reflect(col, v, t, k, m, tol, vb[k1 & 1], &t1, &b1, red, &s_alpha);
-      if (threadIdx.x == 0) {
-        s_tau[k1 & 1] = t1;
-        s_beta = b1;
-      }
-      __syncthreads();
-      publish(k1);
+      apply_then_reflect(col, v, t, k, m, tol, vb[k1 & 1], V + (long long)k1 * m, red, &s_refl);
+      release(k1);
     }
     for (int jj = 0; jj < ncols; ++jj) {
       const int j = c + jj * G;
