@@ -359,11 +359,15 @@ __device__ double2 block_csum_times(double2 v, double2 a, double* red, bool scal
     red[32 + (threadIdx.x >> 5)] = v.y;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double2 s = make_double2(total_of(red), total_of(red + 32));
-    if (scale) s = cmul(a, s);
-    red[16] = s.x;
-    red[48] = s.y;
+  if (threadIdx.x < 2) {  // lane 0 adds the real parts, lane 1 the imaginary ones
+    const double p = total_of(red + 32 * threadIdx.x);
+    const double q = __shfl_sync(0x3u, p, 1);
+    if (threadIdx.x == 0) {
+      double2 s = make_double2(p, q);
+      if (scale) s = cmul(a, s);
+      red[16] = s.x;
+      red[48] = s.y;
+    }
   }
   __syncthreads();
   return make_double2(red[16], red[48]);
@@ -371,6 +375,23 @@ __device__ double2 block_csum_times(double2 v, double2 a, double* red, bool scal
 
 __device__ double2 block_csum(double2 v, double* red) {
   return block_csum_times(v, make_double2(1.0, 0.0), red, false);
+}
+
+// the same sums, with every thread adding the warps' totals itself (no third
+// barrier): the better trade where many blocks share a multiprocessor
+__device__ double2 block_csum_every(double2 v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    red[wid] = v.x;
+    red[32 + wid] = v.y;
+  }
+  __syncthreads();
+  return make_double2(total_of(red), total_of(red + 32));
 }
 
 // sum |A|^2 of the m x n matrix (partial sums per block, fixed grid)
@@ -473,7 +494,8 @@ __global__ void qr_form_q_kernel(const double2* V, const double2* tau, int m, in
     const double2* vk = V + (long long)k * m;
     double2 w = make_double2(0.0, 0.0);
     for (int r = k + threadIdx.x; r < m; r += blockDim.x) w = cfma(cconj(vk[r]), q[r], w);
-    const double2 f = block_csum_times(w, t, red, true);
+    w = block_csum_every(w, red);
+    const double2 f = cmul(t, w);
     for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
       double2 d = cmul(vk[r], f);
       q[r] = make_double2(q[r].x - d.x, q[r].y - d.y);
@@ -492,27 +514,39 @@ struct Refl {
 };
 
 // The block's total of the per-thread squares s and the reflector of a column
-// whose first entry is alpha (read in thread 0 only). Thread 0 forms the
-// scalars once (deflation as in qr_step_kernel) and the block reads them.
+// whose first entry is alpha (read in thread 0 only). Lanes 0..3 of warp 0 form
+// the scalars (deflation as in qr_step_kernel): each adds the same total and
+// takes the same square root, then each takes one of the four independent
+// quotients; thread 0 shares the result with the block.
 __device__ Refl block_reflector(double s, double2 alpha, double tol, double* red, Refl* sr) {
   block_partials(s, red);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 4) {
+    const unsigned lanes = 0xfu;
+    const int l = threadIdx.x;
+    const double ax = __shfl_sync(lanes, alpha.x, 0), ay = __shfl_sync(lanes, alpha.y, 0);
     const double nrm = sqrt(total_of(red));
-    Refl R;
-    R.deflate = (nrm <= tol) || (nrm == 0.0);
-    if (R.deflate) {
-      R.inv = make_double2(0.0, 0.0);
-      R.tau = make_double2(0.0, 0.0);
-      R.beta = alpha;
-    } else {
-      const double b = alpha.x >= 0.0 ? -nrm : nrm;
-      const double2 den = make_double2(alpha.x - b, alpha.y);
-      const double dd = den.x * den.x + den.y * den.y;
-      R.inv = make_double2(den.x / dd, -den.y / dd);
-      R.tau = make_double2((b - alpha.x) / b, -alpha.y / b);
-      R.beta = make_double2(b, 0.0);
+    const double b = ax >= 0.0 ? -nrm : nrm;
+    const double2 den = make_double2(ax - b, ay);
+    const double dd = den.x * den.x + den.y * den.y;
+    // inv = (den.x / dd, -den.y / dd), tau = ((b - ax) / b, -ay / b); unused
+    // (and possibly not finite) when the column deflates
+    const double num = l == 0 ? den.x : l == 1 ? -den.y : l == 2 ? b - ax : -ay;
+    const double q = num / (l < 2 ? dd : b);
+    const double q1 = __shfl_sync(lanes, q, 1), q2 = __shfl_sync(lanes, q, 2), q3 = __shfl_sync(lanes, q, 3);
+    if (l == 0) {
+      Refl R;
+      R.deflate = (nrm <= tol) || (nrm == 0.0);
+      if (R.deflate) {
+        R.inv = make_double2(0.0, 0.0);
+        R.tau = make_double2(0.0, 0.0);
+        R.beta = make_double2(ax, ay);
+      } else {
+        R.inv = make_double2(q, q1);
+        R.tau = make_double2(q2, q3);
+        R.beta = make_double2(b, 0.0);
+      }
+      *sr = R;
     }
-    *sr = R;
   }
   __syncthreads();
   return *sr;
