@@ -3,8 +3,8 @@ fitted back to bond dimension D by variational sweeps, one step after another.
 
 One bench step = one call of evolve_step (all sweeps of one time step, with its
 environment build, QRs, centre and normalisation) on the long-range Ising chain
-L = 100, D = 256, order N = 3 (w = 93), tau = -0.2i, the size the paper's
-method is quoted on for this build. The state lives in HBM across steps; the
+L = 100, D = 256, order N = 3 (w = 93), tau = -0.2i (the headline workload).
+The state lives in HBM across steps; the
 environments (about 9.7 GB in fp64) are larger than L2, so no flush is needed.
 
 Usage:

@@ -14,7 +14,7 @@ Follows arXiv:2302.14181:
   * Algorithm 4 (Sec. 6): approximate compression of the levels without a 1.
   * Eq. boundary (Sec. 3): finite-chain boundaries select level (1,...,1).
 
-Readings of the paper taken here (each also listed in the design doc):
+Readings of the paper taken here:
   * Algorithm 3 loops over the columns b with **no** 1 (the printed "1 in b"
     double counts the (1,1) entry at N = 1; "1 not in b" reproduces both tables
     of the appendix entry by entry).
