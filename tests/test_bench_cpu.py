@@ -1,0 +1,88 @@
+"""Host logic of bench.py, on the CPU.
+
+* step_flops, the useful-flop count behind the bench's TFLOP/s figure, equals 8x
+  the complex multiply-adds of every matmul the oracle's contractions perform in
+  one step (counted while the oracle runs, not re-derived).
+* traffic_from_profiles reports a recorded dram figure only while the kernel's
+  source file still has the recorded hash.
+"""
+import hashlib
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import workloads as wl  # noqa: E402
+from oracle import fit, mpo  # noqa: E402
+
+
+class _Counted(np.ndarray):
+    """ndarray view whose matmuls add M*K*N to a shared counter."""
+
+    counter = None
+
+    def __array_ufunc__(self, ufunc, method, *inputs, **kwargs):
+        args = [np.asarray(x) if isinstance(x, _Counted) else x for x in inputs]
+        if ufunc is np.matmul and method == "__call__":
+            a, b = args
+            assert a.ndim == 2 and b.ndim == 2
+            _Counted.counter[0] += a.shape[0] * a.shape[1] * b.shape[1]
+        out = getattr(ufunc, method)(*args, **kwargs)
+        return out.view(_Counted) if isinstance(out, np.ndarray) else out
+
+
+def _counting(fn):
+    def wrapped(*arrays):
+        out = fn(*[np.asarray(x).view(_Counted) for x in arrays])
+        return np.asarray(out)
+    return wrapped
+
+
+@pytest.mark.parametrize("sweeps", [1, 2])
+@pytest.mark.parametrize("case", [
+    ("xxz_L7_N2_D4", lambda: wl.xxz_blocks(7, 0.5), lambda: wl.product_state("neel", 7), 2, 4),
+    ("lri_L6_N3_D6", lambda: wl.lr_ising_blocks(6, 0.7), lambda: wl.product_state("up", 6), 3, 6),
+])
+def test_step_flops_counts_the_oracle_contractions(monkeypatch, case, sweeps):
+    name, blocks, v0, N, D = case
+    W = mpo.build_mpo(*blocks(), N, -0.1j)
+    psi = fit.product_mps(v0(), D)
+    # one step first, so that the counted step starts from a right-canonical state
+    psi, _ = fit.evolve_step(psi, W, 1, canonical=False)
+    counter = [0]
+    monkeypatch.setattr(_Counted, "counter", counter)
+    for f in ("make_T", "apply_T", "env_next"):
+        monkeypatch.setattr(fit, f, _counting(getattr(fit, f)))
+    fit.evolve_step(psi, W, sweeps, canonical=True)
+    dims = [a.shape[0] for a in psi] + [psi[-1].shape[2]]
+    wl_ = [w.shape[0] for w in W]
+    wr_ = [w.shape[3] for w in W]
+    assert counter[0] > 0
+    assert bench.step_flops(dims, wl_, wr_, psi[0].shape[1], sweeps) == 8.0 * counter[0], name
+
+
+def test_traffic_only_while_source_unchanged(tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        "# kernel bytes hash file\nk_kernel 123456 %s k.cu\nother 1 0000000000000000 k.cu\n" % h)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_from_profiles("k_kernel") == 123456.0
+    assert bench.traffic_from_profiles("other") is None          # recorded for another source
+    assert bench.traffic_from_profiles("missing_kernel") is None
+    src.write_text("__global__ void k() { /* changed */ }\n")
+    assert bench.traffic_from_profiles("k_kernel") is None
+
+
+def test_single_replica_throughput():
+    torch = pytest.importorskip("torch")  # noqa: F841
+    v, ms = bench.replica_throughput(250.0, 2, "cpu")
+    assert ms == 250.0 and v == pytest.approx(8.0)
