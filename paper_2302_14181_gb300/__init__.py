@@ -25,6 +25,7 @@ from ._lib import (FP64, TF32, TF32X3, BF16X3, TC_ONLY, OZAKI, OZAKI_SLICES, MPO
 
 __all__ = [
     "Context", "MPO", "MPS", "mpo_build", "mpo_build_host", "mps_init", "evolve_step", "evolve_step_batched", "measure_local", "mps_overlap",
+    "tevo_gemm", "tevo_gemm_noalloc", "tevo_wait_selftest", "tevo_strerror",
     "FP64", "TF32", "TF32X3", "BF16X3", "TC_ONLY", "OZAKI", "OZAKI_SLICES", "MPO_PLAIN", "MPO_EXACT", "MPO_EXTENDED", "MPO_FULL",
     "TevoError", "library_path",
 ]
@@ -261,3 +262,55 @@ def mps_overlap(a, b):
     la, ph = ctypes.c_double(), ctypes.c_double()
     _lib.check(_lib.lib.mps_overlap(a.handle, b.handle, ctypes.byref(la), ctypes.byref(ph)))
     return la.value, ph.value
+
+
+def _device_matrix(t, name):
+    """(rows, cols, device address) of a C-contiguous 2-D complex128 CUDA tensor."""
+    try:
+        import torch
+    except ImportError as e:  # pragma: no cover - torch is a dependency of the device API
+        raise TypeError(f"{name}: device operands are torch CUDA tensors") from e
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128 and t.dim() == 2
+            and t.is_contiguous()):
+        raise TypeError(f"{name} must be a C-contiguous 2-D complex128 CUDA tensor")
+    return int(t.shape[0]), int(t.shape[1]), int(t.data_ptr())
+
+
+def _gemm_args(A, B, C):
+    M, K, pa = _device_matrix(A, "A")
+    N, KB, pb = _device_matrix(B, "B")
+    MC, NC, pc = _device_matrix(C, "C")
+    if KB != K or (MC, NC) != (M, N):
+        raise ValueError(f"shapes A {M}x{K}, B {N}x{KB}, C {MC}x{NC}: need B N x K and C M x N")
+    return M, N, K, ctypes.c_void_p(pa), ctypes.c_void_p(pb), ctypes.c_void_p(pc)
+
+
+def tevo_gemm(ctx, precision, A, B, C):
+    """C[m, n] = sum_k A[m, k] B[n, k] on the device in the given precision.
+
+    A [M, K], B [N, K] (rows of B, k contiguous) and C [M, N]: C-contiguous
+    complex128 CUDA tensors. Returns C. Synchronises the context's stream."""
+    M, N, K, pa, pb, pc = _gemm_args(A, B, C)
+    _lib.check(_lib.lib.tevo_gemm(ctx.handle, int(precision), M, N, K, pa, pb, pc))
+    return C
+
+
+def tevo_gemm_noalloc(ctx, precision, A, B, C):
+    """tevo_gemm without any device allocation (the library's fixed scratch
+    array; shapes that do not fit it raise TevoError with TEVO_ESHAPE)."""
+    M, N, K, pa, pb, pc = _gemm_args(A, B, C)
+    _lib.check(_lib.lib.tevo_gemm_noalloc(ctx.handle, int(precision), M, N, K, pa, pb, pc))
+    return C
+
+
+def tevo_wait_selftest(ctx, limit_ms):
+    """Run the bounded device-side wait until it gives up after limit_ms.
+    Returns (status, device code); the expected status is TEVO_ETIMEOUT."""
+    code = ctypes.c_int(0)
+    rc = _lib.lib.tevo_wait_selftest(ctx.handle, float(limit_ms), ctypes.byref(code))
+    return rc, code.value
+
+
+def tevo_strerror(code):
+    """Name of a libtevo error code."""
+    return _lib.lib.tevo_strerror(int(code)).decode()

@@ -22,6 +22,25 @@ def test_exports_every_declared_symbol():
 def test_strerror_names_codes():
     for code in range(0, -9, -1):
         assert tv._lib.lib.tevo_strerror(code)
+        assert tv.tevo_strerror(code) == tv._lib.lib.tevo_strerror(code).decode()
+
+
+def test_binding_carries_the_c_names_of_the_compute_entries():
+    for name in ("mpo_build", "mpo_build_host", "mps_init", "evolve_step", "evolve_step_batched",
+                 "measure_local", "mps_overlap", "tevo_gemm", "tevo_gemm_noalloc", "tevo_wait_selftest",
+                 "tevo_strerror"):
+        assert name in tv._lib.declared_symbols(), name
+        assert callable(getattr(tv, name)), name
+
+
+def test_gemm_binding_checks_operands_before_the_library():
+    torch = pytest.importorskip("torch")
+    z = torch.zeros((2, 3), dtype=torch.complex128)   # host memory: refused before any library call
+    for f in (tv.tevo_gemm, tv.tevo_gemm_noalloc):
+        with pytest.raises(TypeError):
+            f(None, tv.FP64, z, z, z)
+        with pytest.raises(TypeError):
+            f(None, tv.FP64, np.zeros((2, 3), np.complex128), z, z)
 
 
 MODELS = {
