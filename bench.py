@@ -468,6 +468,79 @@ def verify(args):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# small, fixed invocations for ncu captures (the commands in profiles/)
+# ----------------------------------------------------------------------------
+
+PROBES = ("kernels", "form", "fp64", "tc", "ozgemm")
+
+
+def probe(args):
+    """One fixed workload per case, on the long-range Ising chain at length
+    --probe-L (the per-site shapes of the L = 100 chain at its interior sites):
+      kernels  every form of evolve_step once from the product state (fp64 with
+               1 sweep; bf16x3, bf16x3 tensor-core only and bf16x3 + Ozaki with
+               2), observables after each, then one overlap;
+      form     two steps of tf32x3 + Ozaki, 2 sweeps each;
+      fp64     one fp64 step, 1 sweep;
+      tc       one bf16x3 and one tf32x3 tensor-core-only step, each from the
+               product state, with --probe-sweeps sweeps;
+      ozgemm   the Ozaki-scheme GEMM alone at the interior-site shapes, timed
+               with the library's events (kernel and slicing per launch)."""
+    import torch
+    import paper_2302_14181_gb300 as tv
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ctx = tv.Context()
+    cfg = wl.config(WORKLOAD, L=args.probe_L)
+    tau, D = cfg["tau"], cfg["D"]
+    W = tv.mpo_build(ctx, *wl.model_blocks(cfg), cfg["N"], tau)
+    v0 = wl.initial_vectors(cfg)
+    X, _, Z = wl.pauli()
+    case = args.probe
+    if case == "kernels":
+        psi = None
+        for prec in (tv.FP64, tv.BF16X3, tv.BF16X3 | tv.TC_ONLY, tv.BF16X3 | tv.OZAKI):
+            psi = tv.mps_init(ctx, v0, D)
+            tv.evolve_step(psi, W, tau, D, 1 if prec == tv.FP64 else 2, prec)
+            tv.measure_local(psi, [X, Z])
+        print(json.dumps({"overlap": tv.mps_overlap(psi, tv.mps_init(ctx, v0, D))}))
+    elif case == "form":
+        psi = tv.mps_init(ctx, v0, D)
+        for _ in range(2):
+            tv.evolve_step(psi, W, tau, D, 2, tv.TF32X3 | tv.OZAKI)
+    elif case == "fp64":
+        psi = tv.mps_init(ctx, v0, D)
+        tv.evolve_step(psi, W, tau, D, 1, tv.FP64)
+    elif case == "tc":
+        for prec in (tv.BF16X3 | tv.TC_ONLY, tv.TF32X3 | tv.TC_ONLY):
+            psi = tv.mps_init(ctx, v0, D)
+            tv.evolve_step(psi, W, tau, D, args.probe_sweeps, prec)
+    elif case == "ozgemm":
+        w, d = W.bond_dims()[cfg["L"] // 2], cfg["d"]
+        rng = np.random.default_rng(0)
+        shapes = {"G1": (D * w, d * D, D), "G3": (d * D, D, w * D), "G3'": (D, w * D, d * D),
+                  "G2": (w * d, D * D, w * d)}
+        for name, (M, N, K) in shapes.items():
+            A = torch.from_numpy(rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))).cuda()
+            B = torch.from_numpy(rng.standard_normal((N, K)) + 1j * rng.standard_normal((N, K))).cuda()
+            C = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+            tv.tevo_gemm(ctx, tv.OZAKI, A, B, C)                    # warm-up
+            ctx.prof_enable(True)
+            for c in (tv._lib.PROF_GEMMOZ, tv._lib.PROF_OZSPLIT):
+                ctx.prof_read(c)
+            for _ in range(5):
+                tv.tevo_gemm(ctx, tv.OZAKI, A, B, C)
+            kms, kn, kfl, _ = ctx.prof_read(tv._lib.PROF_GEMMOZ)
+            sms, sn, _, _ = ctx.prof_read(tv._lib.PROF_OZSPLIT)
+            ctx.prof_enable(False)
+            print(json.dumps({"gemm": name, "M": M, "N": N, "K": K, "kernel_ms": kms / kn,
+                              "executed_tflops": OZ_PAIRS * kfl / (kms / 1e3) / 1e12,
+                              "slicing_ms": sms / max(1, sn)}), flush=True)
+            del A, B, C
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": case, "L": cfg["L"], "launches": ctx.launch_count()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -480,7 +553,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--verify", action="store_true", help="run the t = 5 evolution in each form against the oracle")
     ap.add_argument("--verify-forms", default="bf16x3+oz,tf32x3+oz,fp64+oz,bf16x3,fp64")
+    ap.add_argument("--probe", choices=PROBES, help="run one fixed small workload (for ncu captures) instead")
+    ap.add_argument("--probe-L", type=int, default=20)
+    ap.add_argument("--probe-sweeps", type=int, default=1)
     args = ap.parse_args()
+    if args.probe:
+        probe(args)
+        return
     if args.verify:
         verify(args)
         return
