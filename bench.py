@@ -472,7 +472,7 @@ def verify(args):
 # small, fixed invocations for ncu captures (the commands in profiles/)
 # ----------------------------------------------------------------------------
 
-PROBES = ("kernels", "form", "fp64", "tc", "ozgemm")
+PROBES = ("kernels", "form", "fp64", "tc", "ozgemm", "qr")
 
 
 def probe(args):
@@ -486,7 +486,10 @@ def probe(args):
       tc       one bf16x3 and one tf32x3 tensor-core-only step, each from the
                product state, with --probe-sweeps sweeps;
       ozgemm   the Ozaki-scheme GEMM alone at the interior-site shapes, timed
-               with the library's events (kernel and slicing per launch)."""
+               with the library's events (kernel and slicing per launch);
+      qr       two untimed steps of tf32x3 + Ozaki, then three steps with the
+               library's events on: QR factorisation and Q formation time per
+               step and per call."""
     import torch
     import paper_2302_14181_gb300 as tv
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -537,6 +540,25 @@ def probe(args):
                               "executed_tflops": OZ_PAIRS * kfl / (kms / 1e3) / 1e12,
                               "slicing_ms": sms / max(1, sn)}), flush=True)
             del A, B, C
+    elif case == "qr":
+        psi = tv.mps_init(ctx, v0, D)
+        for _ in range(2):
+            tv.evolve_step(psi, W, tau, D, 2, tv.TF32X3 | tv.OZAKI)
+        torch.cuda.synchronize()
+        ctx.prof_enable(True)
+        for c in (tv._lib.PROF_QR, tv._lib.PROF_FORMQ):
+            ctx.prof_read(c)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            tv.evolve_step(psi, W, tau, D, 2, tv.TF32X3 | tv.OZAKI)
+        torch.cuda.synchronize()
+        step_s = (time.perf_counter() - t0) / 3
+        qms, qn, _, _ = ctx.prof_read(tv._lib.PROF_QR)
+        fms, fn, _, _ = ctx.prof_read(tv._lib.PROF_FORMQ)
+        ctx.prof_enable(False)
+        print(json.dumps({"step_s": step_s, "qr_ms_per_step": qms / 3, "qr_calls_per_step": qn / 3,
+                          "qr_ms_per_call": qms / max(1, qn), "form_q_ms_per_step": fms / 3,
+                          "form_q_ms_per_call": fms / max(1, fn)}), flush=True)
     torch.cuda.synchronize()
     print(json.dumps({"probe": case, "L": cfg["L"], "launches": ctx.launch_count()}), flush=True)
 
