@@ -86,3 +86,34 @@ def test_single_replica_throughput():
     torch = pytest.importorskip("torch")  # noqa: F841
     v, ms = bench.replica_throughput(250.0, 2, "cpu")
     assert ms == 250.0 and v == pytest.approx(8.0)
+
+
+def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
+    import json
+    from types import SimpleNamespace
+    orig = bench.oracle_sample
+    # the oracle timed as it stands, on a small interior shape so the test is quick
+    monkeypatch.setattr(bench, "oracle_sample",
+                        lambda cfg, seconds=0.0, seed=7: orig(dict(cfg, D=16), seconds=0.0, seed=seed))
+    monkeypatch.delenv("RANK", raising=False)
+    bench.reference_arm(SimpleNamespace(warmup=1, steps=2, gpus=1))
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "sweeps/s"
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "sweeps/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == bench.WORKLOAD
+
+
+def test_reference_arm_is_silent_off_rank_zero(monkeypatch, capsys):
+    from types import SimpleNamespace
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: pytest.fail("rank 1 must not run the oracle"))
+    bench.reference_arm(SimpleNamespace(warmup=1, steps=1, gpus=2))
+    assert capsys.readouterr().out == ""
