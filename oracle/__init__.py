@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY. Nothing in the product path may import, call, link or
 execute this package: only the tests, ``__graft_entry__.smoke()`` and the CPU
-baseline leg of ``bench.py`` use it. It shares no code with the CUDA library.
+legs of ``bench.py`` (``cpu_baseline`` and ``--impl reference``) use it. It shares no code with the CUDA library.
 
 Plain, slow, fp64-complex CPU code, written from the paper:
 
