@@ -58,7 +58,8 @@ extern "C" {
  * TEVO_FP64) are computed on the bf16 tensor cores by the Ozaki splitting
  * scheme: each operand row is scaled by a power of two and cut into integer
  * digit slices of 7 bits, digit products are exact and their sums are exact in
- * the fp32 accumulator, and the pass results are scaled and summed in fp64.
+ * the fp32 accumulator, and the pass results are summed per entry in 64-bit
+ * fixed point (integer instructions) and rounded once to fp64.
  * With G slices the dropped part is about (G + 2) 2^(-7 G) of
  * max|row of A| max|row of B| K per entry (G = 8: 56 bits; a native fp64 GEMM
  * has about K 2^-53 of sum |A||B|). Inputs, outputs, the QR, the norm and the
