@@ -117,3 +117,62 @@ def test_reference_arm_is_silent_off_rank_zero(monkeypatch, capsys):
     monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: pytest.fail("rank 1 must not run the oracle"))
     bench.reference_arm(SimpleNamespace(warmup=1, steps=1, gpus=2))
     assert capsys.readouterr().out == ""
+
+
+def test_probe_cases_issue_their_calls(monkeypatch, capsys):
+    """The fixed workloads behind the ncu captures in profiles/ (bench.py --probe),
+    run against a stand-in of the binding that records the calls."""
+    import types
+    torch = pytest.importorskip("torch")
+    calls = []
+
+    class Handle:
+        def bond_dims(self):
+            return [1] + [93] * 19 + [1]
+
+        def prof_enable(self, on=True):
+            pass
+
+        def prof_read(self, c):
+            return (1.0, 5, 1e12, 0.0)
+
+        def launch_count(self, reset=False):
+            return 0
+
+    fake = types.ModuleType("paper_2302_14181_gb300")
+    fake.FP64, fake.TF32, fake.TF32X3, fake.BF16X3, fake.TC_ONLY, fake.OZAKI = 0, 1, 2, 3, 0x100, 0x200
+    fake._lib = types.SimpleNamespace(PROF_GEMMOZ=4, PROF_OZSPLIT=5, PROF_QR=2, PROF_FORMQ=3)
+    fake.Context = lambda: Handle()
+    fake.mpo_build = lambda ctx, *a: Handle()
+    fake.mps_init = lambda ctx, v0, D: (calls.append(("init", D)), Handle())[1]
+    fake.evolve_step = lambda psi, W, tau, D, sweeps, prec: calls.append(("step", sweeps, prec))
+    fake.measure_local = lambda psi, ops: calls.append(("measure",))
+    fake.mps_overlap = lambda a, b: (0.0, 0.0)
+    fake.tevo_gemm = lambda ctx, prec, A, B, C: calls.append(("gemm", tuple(A.shape), tuple(B.shape)))
+    monkeypatch.setitem(sys.modules, "paper_2302_14181_gb300", fake)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self: self)
+    zeros = torch.zeros
+    monkeypatch.setattr(torch, "zeros", lambda *a, **k: zeros(*a, **{x: v for x, v in k.items() if x != "device"}))
+    from types import SimpleNamespace
+    expect = {
+        "kernels": [("init", 256), ("step", 1, 0), ("measure",), ("init", 256), ("step", 2, 3), ("measure",),
+                    ("init", 256), ("step", 2, 0x103), ("measure",), ("init", 256), ("step", 2, 0x203),
+                    ("measure",), ("init", 256)],
+        "form": [("init", 256), ("step", 2, 0x202), ("step", 2, 0x202)],
+        "fp64": [("init", 256), ("step", 1, 0)],
+        "tc": [("init", 256), ("step", 1, 0x103), ("init", 256), ("step", 1, 0x102)],
+        "qr": [("init", 256)] + [("step", 2, 0x202)] * 5,
+    }
+    for case in bench.PROBES:
+        calls.clear()
+        bench.probe(SimpleNamespace(probe=case, probe_L=20, probe_sweeps=1))
+        if case == "ozgemm":
+            shapes = sorted({c[1:] for c in calls})
+            assert shapes == sorted({((23808, 256), (512, 256)), ((512, 23808), (256, 23808)),
+                                     ((256, 512), (23808, 512)), ((186, 186), (65536, 186))}), shapes
+            assert len(calls) == 4 * 6                   # one warm-up and five timed calls per shape
+        else:
+            assert calls == expect[case], case
+    assert '"probe": "qr"' in capsys.readouterr().out
