@@ -243,7 +243,12 @@ int tevo_gemm(tevo_ctx ctx, int precision, int M, int N, int K, const double* A,
  *  - Every call uses the same array and leaves its contents behind; the call
  *    clears what must start at zero. Calls whose GPU work overlaps -- on two
  *    streams, or from two host threads -- race on the array: serialise them.
- * Arguments, layouts and errors as for tevo_gemm. Synchronises the context stream.
+ *  - The context's device must be the current device (else TEVO_EINVAL): the
+ *    array's address differs per device.
+ * Arguments and layouts as for tevo_gemm, except that precision is one of
+ * TEVO_FP64, TEVO_TF32, TEVO_TF32X3 or TEVO_BF16X3: the Ozaki flag (and any
+ * other flag bit) is refused with TEVO_EINVAL. Errors: TEVO_EINVAL, TEVO_ESHAPE,
+ * TEVO_ECUDA, TEVO_ETIMEOUT. Synchronises the context stream.
  */
 #define TEVO_NOALLOC_SCRATCH_BYTES (64u << 20)
 int tevo_gemm_noalloc(tevo_ctx ctx, int precision, int M, int N, int K, const double* A, const double* B,

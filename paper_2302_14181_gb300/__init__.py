@@ -297,8 +297,14 @@ def tevo_gemm(ctx, precision, A, B, C):
 
 def tevo_gemm_noalloc(ctx, precision, A, B, C):
     """tevo_gemm without any device allocation (the library's fixed scratch
-    array; shapes that do not fit it raise TevoError with TEVO_ESHAPE)."""
+    array; shapes that do not fit it raise TevoError with TEVO_ESHAPE). A, B and
+    C must sit on the context's device, which must be current."""
     M, N, K, pa, pb, pc = _gemm_args(A, B, C)
+    import torch
+    cur = torch.cuda.current_device()
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        if t.device.index != cur:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{cur}")
     _lib.check(_lib.lib.tevo_gemm_noalloc(ctx.handle, int(precision), M, N, K, pa, pb, pc))
     return C
 

@@ -1243,7 +1243,7 @@ extern "C" int tevo_gemm_noalloc(tevo_ctx c, int precision, int M, int N, int K,
   if (precision < TEVO_FP64 || precision > TEVO_BF16X3) return TEVO_EINVAL;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15)
     return TEVO_EINVAL;
-  return noalloc_gemm(launch_of(c), precision, M, N, K, A, B, C);
+  return noalloc_gemm(launch_of(c), c->device, precision, M, N, K, A, B, C);
 }
 
 extern "C" int tevo_wait_selftest(tevo_ctx c, double limit_ms, int* code) {

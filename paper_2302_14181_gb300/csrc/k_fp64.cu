@@ -271,13 +271,8 @@ int zsparse_g2(const Launch& L, const z64* X, z64* T, const int* row_ptr, const 
   while (BW > 8 && (size_t)K * BW * sizeof(double2) > 200 * 1024) BW /= 2;
   const size_t smem = (size_t)K * BW * sizeof(double2);
   if (smem > 220 * 1024) return TEVO_EUNSUPPORTED;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(zsparse_g2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) !=
-        cudaSuccess)
-      return TEVO_ECUDA;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (smem_attr_once(zsparse_g2_kernel, 220 * 1024, attr)) return TEVO_ECUDA;
   if (batch > 65535) return TEVO_ESHAPE;
   dim3 grid((Db + BW - 1) / BW, batch);
   zsparse_g2_kernel<<<grid, 256, smem, L.stream>>>(reinterpret_cast<const double2*>(X), reinterpret_cast<double2*>(T),
@@ -776,12 +771,9 @@ int qr64_factor(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_, z64*
   *L.launches += 2;
   const size_t smem = sizeof(double2) * (size_t)m;
   if (smem > 48 * 1024) {
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaFuncSetAttribute(qr_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      cudaFuncSetAttribute(qr_form_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_step{0}, attr_q{0};
+    if (smem_attr_once(qr_step_kernel, 200 * 1024, attr_step) || smem_attr_once(qr_form_q_kernel, 200 * 1024, attr_q))
+      return TEVO_ECUDA;
   }
   for (int k = 0; k < n; ++k) {
     int grid = n - k - 1;
@@ -803,12 +795,8 @@ int qr64_factor_coop(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_,
   const int ncols = (n + G - 1) / G;
   const size_t smem = sizeof(double2) * (size_t)(ncols + 2) * m;
   if (smem > 200 * 1024) return TEVO_EUNSUPPORTED;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(qr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
-      return TEVO_ECUDA;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (smem_attr_once(qr_coop_kernel, 200 * 1024, attr)) return TEVO_ECUDA;
   // every CTA must be resident at once: check the occupancy for this size
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_coop_kernel, 256, smem) != cudaSuccess ||
@@ -832,6 +820,9 @@ int qr64_factor_coop(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_,
 int qr64_form_q(const Launch& L, const z64* V, const z64* tau, int m, int n, z64* Q, long long sQr,
                 long long sQc) {
   const size_t smem = sizeof(double2) * (size_t)m;
+  if (smem > 200 * 1024) return TEVO_EUNSUPPORTED;
+  static std::atomic<unsigned long long> attr{0};
+  if (smem > 48 * 1024 && smem_attr_once(qr_form_q_kernel, 200 * 1024, attr)) return TEVO_ECUDA;
   const double fflops = 8.0 * (4.0 * (double)m * n * n - 4.0 / 3.0 * (double)n * n * n) / 2.0;
   int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_FORMQ, fflops, 32.0 * (double)m * n) : -1;
   qr_form_q_kernel<<<n, QR_THREADS, smem, L.stream>>>(reinterpret_cast<const double2*>(V),

@@ -70,14 +70,6 @@ constexpr int OZ_SMEM_BYTES = OZ_NSTAGE * OZ_STAGE_BYTES + 1024 /*align*/ + 256 
 constexpr int OZ_EPI_WARPS = OZ_EPILOGUE_WARPS;
 static_assert(OZ_EPI_WARPS == 4 || OZ_EPI_WARPS == 8, "epilogue warps");
 constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
-// CTAs per cluster: the CTAs of a cluster work on neighbouring row tiles of the
-// same column tile, and each loads half of the shared B tile by TMA multicast
-#ifndef OZ_CLUSTER_SIZE
-#define OZ_CLUSTER_SIZE 2
-#endif
-constexpr int OZ_CL = OZ_CLUSTER_SIZE;
-static_assert(OZ_CL == 1 || OZ_CL == 2, "cluster size");
-
 // one operand to cut into digit slices: element (r, k) of R x K at
 // src[(r / R2) * sR1 + (r % R2) * sR + k * sK] (conjugated when conj), digit
 // planes written to dst[p * plane_stride + r * row_pitch + k], the row maxima
@@ -115,36 +107,6 @@ struct OzArgs {
   int base_shift;  // S unit: 2^-base_shift of a group-0 pass value
   int* err;
 };
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// TMA tile load whose data and completion signal go to the same offsets in the
-// shared memory of every CTA of the cluster named in mask
-__device__ __forceinline__ void tma_load_4d_mc(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
-                                               uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
-      "%3, %4, %5}], [%6], %7;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar), "h"(mask)
-      : "memory");
-}
-
-// arrive on the mbarrier at this offset in every CTA of mask once the MMAs
-// issued so far have completed
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                   bar),
-               "h"(mask)
-               : "memory");
-}
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile(
@@ -376,8 +338,7 @@ __global__ void oz_reduce_kernel(const double2* P, int splits, int M, int N, dou
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmBh, OzArgs a) {
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_NSTAGE * OZ_STAGE_BYTES);
@@ -388,17 +349,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
   const int mt = (a.M + OZ_TM - 1) / OZ_TM, nt = (a.N + OZ_TN - 1) / OZ_TN;
-  // a unit is a group of OZ_CL row tiles x one column tile x one split; the CTAs
-  // of a cluster take its row tiles (past the last row tile: zero rows)
-  const int mtc = (mt + OZ_CL - 1) / OZ_CL;
-  const int nunits = mtc * nt * a.splits;
-  const int crank = OZ_CL > 1 ? (int)cluster_rank() : 0;
-  const int cid = blockIdx.x / OZ_CL, ncl = gridDim.x / OZ_CL;
+  // a unit is one row tile x one column tile x one split
+  const int nunits = mt * nt * a.splits;
+  const int cid = blockIdx.x, ncl = gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_NSTAGE; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, OZ_CL);  // a stage is free once every CTA of the cluster used it
+      mbar_init(empty0 + 8 * s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
@@ -406,8 +364,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // the partner's barriers must exist before any multicast reaches them
-  if (OZ_CL > 1) cluster_sync();
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(512));
@@ -422,9 +378,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   // the shorter tile dimension runs fastest, so CTAs that run together share
   // the tiles of the longer operand (read once from DRAM, then from L2)
   auto unit_of = [&](int u, int& m0, int& n0, int& c0, int& c1) {
-    const int z = u / (mtc * nt), r = u % (mtc * nt);
-    m0 = ((mtc <= nt ? r % mtc : r / nt) * OZ_CL + crank) * OZ_TM;
-    n0 = (mtc <= nt ? r / mtc : r % nt) * OZ_TN;
+    const int z = u / (mt * nt), r = u % (mt * nt);
+    m0 = (mt <= nt ? r % mt : r / nt) * OZ_TM;
+    n0 = (mt <= nt ? r / mt : r % nt) * OZ_TN;
     c0 = z * a.cps;
     c1 = min(a.nchunks, c0 + a.cps);
     return z;
@@ -442,8 +398,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(OZ_CL == 1 ? &tmB : &tmBh))
-                   : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
       long long q = 0;  // stage ring counter
       bool ok = true;
       for (int u = cid; u < nunits && ok; u += ncl) {
@@ -464,15 +419,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 mbar_expect_tx(fb, OZ_STAGE_BYTES);
                 uint8_t* sp = smem + st * OZ_STAGE_BYTES;
                 tma_load_4d(smem_u32(sp), &tmA, kt * 32, 0, m0, 2 * s, fb);
-                if (OZ_CL == 1) {
-                  tma_load_4d(smem_u32(sp + OZ_A_BYTES), &tmB, kt * 32, 0, n0, 2 * (g - s), fb);
-                } else {
-                  // this CTA's half of the B rows, both planes, into every CTA of the cluster
-                  const uint32_t hb = smem_u32(sp + OZ_A_BYTES) + (uint32_t)(crank * (OZ_TN / 2) * OZ_KCB);
-                  const int nh = n0 + crank * (OZ_TN / 2);
-                  tma_load_4d_mc(hb, &tmBh, kt * 32, 0, nh, 2 * (g - s), fb, (uint16_t)0x3);
-                  tma_load_4d_mc(hb + OZ_TN * OZ_KCB, &tmBh, kt * 32, 0, nh, 2 * (g - s) + 1, fb, (uint16_t)0x3);
-                }
+                tma_load_4d(smem_u32(sp + OZ_A_BYTES), &tmB, kt * 32, 0, n0, 2 * (g - s), fb);
               }
       }
       // do not leave while copies are in flight
@@ -525,10 +472,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                   mma<TC_BF16>(dim, ar + plane_a + o, br + o, idesc, 1u);              // Im += Ai Br
                   first = false;
                 }
-                if (OZ_CL == 1)
-                  mma_commit(empty0 + 8 * st);
-                else
-                  mma_commit_mc(empty0 + 8 * st, (uint16_t)0x3);  // the stage holds the partner's B half too
+                mma_commit(empty0 + 8 * st);
               }
             mma_commit(tfull0 + 8 * b);
           }
@@ -616,8 +560,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
-  // no CTA leaves while its partner may still write into its shared memory
-  if (OZ_CL > 1) cluster_sync();
 }
 
 inline size_t al256(size_t b) { return (b + 255) / 256 * 256; }
@@ -649,10 +591,9 @@ OzPlan plan(int M, int N, int K, int G, int num_sms) {
   p.b_bytes = al256((size_t)2 * G * N * kp * 2);
   p.e_bytes = al256((size_t)(M + N) * (sizeof(int) + sizeof(unsigned long long)));
   p.p_bytes = p.splits > 1 ? al256((size_t)p.splits * M * N * 16) : 0;
-  // persistent grid: whole clusters, one CTA per SM at most
-  const long long cunits =
-      (long long)((M + OZ_TM * OZ_CL - 1) / (OZ_TM * OZ_CL)) * ((N + OZ_TN - 1) / OZ_TN) * p.splits;
-  p.grid = OZ_CL * (int)std::max<long long>(1, std::min<long long>(cunits, (long long)(num_sms / OZ_CL)));
+  // persistent grid: one CTA per SM at most
+  const long long units = (long long)((M + OZ_TM - 1) / OZ_TM) * ((N + OZ_TN - 1) / OZ_TN) * p.splits;
+  p.grid = (int)std::max<long long>(1, std::min<long long>(units, (long long)num_sms));
   p.s_bytes = al256((size_t)p.grid * OZ_TM * OZ_TN * sizeof(longlong2));
   // |pass value| <= 2^24 and sum_g 2^-W g < 1.008: cps chunks stay below
   // 2^(base_shift + 24 + log2 cps + 0.02) <= 2^62.02 < 2^63
@@ -707,13 +648,8 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
   if (slices < 1 || slices > OZ_MAX_SLICES) return TEVO_EINVAL;
   if (g.M <= 0 || g.N <= 0) return 0;
   if (g.K <= 0) return TEVO_EUNSUPPORTED;
-  static bool attr_done = false;
-  if (!attr_done) {
-    if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES) !=
-        cudaSuccess)
-      return TEVO_ECUDA;
-    attr_done = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  if (smem_attr_once(oz_gemm_kernel, OZ_SMEM_BYTES, attr_done)) return TEVO_ECUDA;
   const OzPlan p = plan(g.M, Nt, g.K, slices, L.num_sms);
   if (!ws || !err || ws_bytes < p.total()) return TEVO_ESHAPE;
   char* w = static_cast<char*>(ws);
@@ -746,10 +682,9 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
 
   TcOperand oa{da, 2, 2 * slices, (long long)g.M * kp, g.M, kp, g.K, 1, kp};
   TcOperand ob{db, 2, 2 * slices, (long long)Nt * kp, Nt, kp, g.K, 1, kp};
-  CUtensorMap ma, mb, mbh;
+  CUtensorMap ma, mb;
   e = tc_make_map(&ma, oa, OZ_TM, 2);
   if (!e) e = tc_make_map(&mb, ob, OZ_TN, 2);
-  if (!e) e = tc_make_map(&mbh, ob, OZ_TN / 2, 1);  // half a B tile, one plane (multicast loads)
   if (e) return e;
   OzArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -777,20 +712,8 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
   const int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_GEMMOZ, useful,
                                         16.0 * ((double)g.M * g.K + (double)Nt * g.K + (double)g.M * Nt))
                         : -1;
-  cudaLaunchConfig_t cfg;
-  std::memset(&cfg, 0, sizeof(cfg));
-  cfg.gridDim = dim3((unsigned)p.grid);
-  cfg.blockDim = dim3(OZ_THREADS);
-  cfg.dynamicSmemBytes = OZ_SMEM_BYTES;
-  cfg.stream = L.stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = OZ_CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, oz_gemm_kernel, ma, mb, mbh, a) != cudaSuccess) return TEVO_ECUDA;
+  oz_gemm_kernel<<<p.grid, OZ_THREADS, OZ_SMEM_BYTES, L.stream>>>(ma, mb, a);
+  if (cudaGetLastError() != cudaSuccess) return TEVO_ECUDA;
   ++*L.launches;
   if (p.splits > 1) {
     oz_reduce_kernel<<<grid_of((long long)g.M * Nt, 256, L.num_sms), 256, 0, L.stream>>>(

@@ -447,16 +447,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once (a function-local static is initialised once, thread-safely)
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -510,18 +509,12 @@ void tc_products(int fmt, TcArgs& a) {
 }
 
 int tc_gemm(const Launch& L, int fmt, const TcOperand& A, const TcOperand& B, int M, int N, TcArgs args) {
-  static bool attr_done[3] = {false, false, false};
+  static std::atomic<unsigned long long> attr_done[3];
   const int kind = fmt == TC_BF16 ? 0 : (fmt == TC_TF32X3 ? 1 : 2);
-  if (!attr_done[kind]) {
-    cudaError_t e = kind == 0   ? cudaFuncSetAttribute(tc_gemm_kernel<TC_BF16, 12>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
-                    : kind == 1 ? cudaFuncSetAttribute(tc_gemm_kernel<TC_TF32, 12>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
-                                : cudaFuncSetAttribute(tc_gemm_kernel<TC_TF32, 4>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return TEVO_ECUDA;
-    attr_done[kind] = true;
-  }
+  const int ae = kind == 0   ? smem_attr_once(tc_gemm_kernel<TC_BF16, 12>, SMEM_BYTES, attr_done[0])
+                 : kind == 1 ? smem_attr_once(tc_gemm_kernel<TC_TF32, 12>, SMEM_BYTES, attr_done[1])
+                             : smem_attr_once(tc_gemm_kernel<TC_TF32, 4>, SMEM_BYTES, attr_done[2]);
+  if (ae) return TEVO_ECUDA;
   if (A.k_in != B.k_in || A.k_out != B.k_out || A.planes != B.planes || A.elem_bytes != B.elem_bytes)
     return TEVO_ESHAPE;
   if (A.rows < M || B.rows < N) return TEVO_ESHAPE;

@@ -25,11 +25,15 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-// device address of the scratch array for the current device (host code may not
-// use the symbol itself as an address); looked up once per device
-int scratch_for_current_device(void** out) {
+// device address of the scratch array on the context's device (host code may
+// not use the symbol itself as an address); looked up once per device, with
+// that device current. The context's kernels run on its stream, so a call made
+// while another device is current is refused: the address would belong to the
+// other device's copy of the array.
+int scratch_for_device(int ctx_device, void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return TEVO_ECUDA;
+  if (dev != ctx_device) return TEVO_EINVAL;
   if (dev < 0 || dev >= kMaxDevices) return TEVO_EUNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_ptr[dev]) {
@@ -90,9 +94,10 @@ size_t noalloc_need(int precision, int M, int N, int K, int num_sms, int* splits
   return 256 + planes + al256((size_t)splits * M * N * 8);
 }
 
-int noalloc_gemm(const Launch& L, int precision, int M, int N, int K, const void* A, const void* B, void* C) {
+int noalloc_gemm(const Launch& L, int device, int precision, int M, int N, int K, const void* A, const void* B,
+                 void* C) {
   void* base = nullptr;
-  TRY_NA(scratch_for_current_device(&base));
+  TRY_NA(scratch_for_device(device, &base));
   int splits = 1;
   const size_t need = noalloc_need(precision, M, N, K, L.num_sms, &splits);
   if (need == 0 || need > (size_t)TEVO_NOALLOC_SCRATCH_BYTES) return TEVO_ESHAPE;

@@ -10,6 +10,8 @@
 
 #ifdef __CUDACC__
 #include <cuda_runtime.h>
+
+#include <atomic>
 #else
 struct CUstream_st;
 typedef CUstream_st* cudaStream_t;
@@ -69,6 +71,25 @@ struct Launch {
   int num_sms;
   Prof* prof;
 };
+
+#ifdef __CUDACC__
+// Raise a kernel's dynamic shared-memory limit on the current device. The
+// attribute is kept per device, so `done` holds one bit per device (devices
+// 0..63; higher ones set it on every call). Concurrent first calls may both set
+// it, which is harmless.
+template <typename F>
+inline int smem_attr_once(F* kernel, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TEVO_ECUDA;
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return 0;
+  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(kernel), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           bytes) != cudaSuccess)
+    return TEVO_ECUDA;
+  done.fetch_or(bit, std::memory_order_release);
+  return 0;
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // fp64 kernels (k_fp64.cu)

@@ -24,7 +24,8 @@ int mixed_error_flag(tevo_ctx c, tevo_mps s, int* flag);
 // standalone complex GEMM (tevo_gemm)
 int mixed_gemm(tevo_ctx c, int precision, int M, int N, int K, const void* A, const void* B, void* C);
 // tevo_gemm_noalloc (noalloc.cu)
-int noalloc_gemm(const Launch& L, int precision, int M, int N, int K, const void* A, const void* B, void* C);
+int noalloc_gemm(const Launch& L, int device, int precision, int M, int N, int K, const void* A, const void* B,
+                 void* C);
 void mixed_mpo_destroy(tevo_ctx c, MixedMPO*& m);
 void mixed_state_destroy(tevo_ctx c, MixedState*& m);
 
