@@ -182,7 +182,8 @@ def dtype_of(form):
     if form == "fp64":
         return "c128"
     if form == "fp64+oz":
-        return "c128 in/out; contractions as exact bf16 digit-slice products (Ozaki, 8 slices), fixed-point sums"
+        return ("c128 in/out; every contraction as exact bf16 digit-slice products on the tensor cores (Ozaki, "
+                "8 slices) with exact fixed-point sums, rounded once to f64; c128 QR and reductions")
     base = form.replace("tc-", "").replace("+oz", "")
     if form.startswith("tc-"):
         return f"{base} contractions + c128 QR"
@@ -323,18 +324,25 @@ def our_arm(args):
             got = tv.measure_local(psi, list(wl.pauli())).real
             obs_err = {"step": nstep, "t": nstep * abs(tau), "max_abs": float(np.abs(got - ref).max()),
                        "against": "fp64 oracle (tests/golden)"}
-    # the plain fp64 form, one step from the same state, for the mixed-vs-fp64 comparison
-    fp64_form = None
-    if prec != 0 and not args.no_fp64_compare:
-        barrier()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        tv.evolve_step(psi, W, tau, D, sweeps, tv.FP64)
-        f1.record(stream)
-        barrier()
-        fms = f0.elapsed_time(f1)
-        fp64_form = {"value": sweeps / (fms / 1e3), "unit": "sweeps/s", "ms_per_step": fms, "sweeps": sweeps,
-                     "speedup_of_measured_form": (fms / (ms_max / args.steps))}
+    # the other forms, one step each from the same state: the plain fp64 form
+    # (the comparison the metric names) and the tensor-core sweep forms (one
+    # bf16x3 sweep, then an fp64 sweep: native, or as Ozaki-scheme GEMMs)
+    fp64_form, other_forms = None, {}
+    if not args.no_fp64_compare:
+        for name in ("fp64", "bf16x3", "bf16x3+oz", "fp64+oz"):
+            if PREC[name] == prec:
+                continue
+            barrier()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            tv.evolve_step(psi, W, tau, D, sweeps, PREC[name])
+            f1.record(stream)
+            barrier()
+            fms = f0.elapsed_time(f1)
+            other_forms[name] = {"value": sweeps / (fms / 1e3), "unit": "sweeps/s", "ms_per_step": fms,
+                                 "sweeps": sweeps, "dtype": dtype_of(name),
+                                 "speedup_of_measured_form": (fms / (ms_max / args.steps))}
+        fp64_form = other_forms.get("fp64")
 
     # end to end through the public API with host buffers (pinned), every step:
     # upload the state, evolve, read observables and the state back
@@ -426,6 +434,7 @@ def our_arm(args):
             "gpu_launches": launches,
             "obs_error": obs_err,
             "fp64_form": fp64_form,
+            "other_forms": other_forms,
             "clocks": clocks.summary(),
             "kernel_ms": {name: prof[c][0] for c, name in enumerate(PROF_NAMES)},
         }
@@ -569,8 +578,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("TEVO_BENCH_PRECISION", "bf16x3+oz"), choices=sorted(PREC))
-    ap.add_argument("--no-fp64-compare", action="store_true", help="skip the fp64-form step timed beside the mixed form")
+    ap.add_argument("--precision", default=os.environ.get("TEVO_BENCH_PRECISION", "fp64+oz"), choices=sorted(PREC))
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the steps of the other forms timed beside the measured one")
     ap.add_argument("--sweeps", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--verify", action="store_true", help="run the t = 5 evolution in each form against the oracle")

@@ -58,8 +58,9 @@ extern "C" {
  * TEVO_FP64) are computed on the bf16 tensor cores by the Ozaki splitting
  * scheme: each operand row is scaled by a power of two and cut into integer
  * digit slices of 7 bits, digit products are exact and their sums are exact in
- * the fp32 accumulator, and the pass results are summed per entry in 64-bit
- * fixed point (integer instructions) and rounded once to fp64.
+ * the fp32 accumulator, and the pass results are summed per entry exactly in
+ * two 64-bit fixed-point accumulators (integer instructions; 128 bits of
+ * range together) and rounded once to fp64.
  * With G slices the dropped part is about (G + 2) 2^(-7 G) of
  * max|row of A| max|row of B| K per entry (G = 8: 56 bits; a native fp64 GEMM
  * has about K 2^-53 of sum |A||B|). Inputs, outputs, the QR, the norm and the
@@ -73,7 +74,7 @@ extern "C" {
 #define TEVO_MPO_PLAIN 0     /* Algorithm 1 only (Eq. W1 at N = 1, Eq. W2 at N = 2) */
 #define TEVO_MPO_EXACT 1     /* Algorithms 1 + 2 */
 #define TEVO_MPO_EXTENDED 2  /* Algorithms 3 + 1 + 2 */
-#define TEVO_MPO_FULL 3      /* Algorithms 3 + 1 + 2 + 4: the order-N MPO of the Sec. 7.3 table */
+#define TEVO_MPO_FULL 3      /* Algorithms 3 + 1 + 2 + 4: the order-N MPO of the Sec. 8.3 table */
 
 typedef struct tevo_ctx_s* tevo_ctx;
 typedef struct tevo_mpo_s* tevo_mpo;
@@ -152,7 +153,7 @@ int mps_destroy(tevo_mps psi);
 /*
  * evolve_step -- one time step psi <- W psi / ||W psi||, fitted at psi's bond
  * dimensions by variational sweeps (Sec. 2.2 and Table 1, "(i)DMRG" row; the
- * set-up of Sec. 7.2: one variational fit per time step at fixed bond
+ * set-up of Sec. 8.2: one variational fit per time step at fixed bond
  * dimension).
  *
  * The step starts from phi = psi (right-canonical), builds the right
@@ -195,7 +196,7 @@ int evolve_step_batched(tevo_mps* psis, const tevo_mpo* Ws, int n, int sweeps, i
 
 /*
  * measure_local -- <O_i> = <psi|O_i|psi>/<psi|psi> for every site i and each of
- * nops single-site operators (the local observables of Sec. 7.2), in any gauge.
+ * nops single-site operators (the local observables of Sec. 8.2), in any gauge.
  * ops: complex [nops][d][d] host; out: complex [nops][L] host.
  * Errors: TEVO_EINVAL, TEVO_ENOMEM, TEVO_ECUDA. Synchronises the stream.
  */

@@ -9,7 +9,7 @@ Plain, slow, fp64-complex CPU code, written from the paper:
 * ``oracle.mpo``   -- powers of the Hamiltonian MPO (Sec. 2.5) and Algorithms 1-4
                       (Secs. 3-6) giving the order-N MPO W^(N)(tau), densified per site.
 * ``oracle.fit``   -- single-site variational fit of W|psi> back to bond dimension D
-                      (Sec. 2.2, Table 1 "(i)DMRG" row; benchmark set-up of Sec. 7.2),
+                      (Sec. 2.2, Table 1 "(i)DMRG" row; benchmark set-up of Sec. 8.2),
                       Householder QR, local expectation values, overlaps.
 * ``oracle.dense`` -- dense references for small chains: H from the finite-state
                       expansion of Sec. 2.3, the dense MPO, exp(tau H) by eigh.

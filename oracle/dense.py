@@ -8,7 +8,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
     matrix with the boundary vectors of Eq. boundary already sliced in.
   * ``expm_tau_h`` is exp(tau H) from numpy.linalg.eigh of the Hermitian H.
 
-Pins: tests/test_oracle_dense.py checks the expansion against Kronecker-sum
+Pins: tests/test_oracle_fit.py checks the expansion against Kronecker-sum
 Hamiltonians written directly from the model definitions, and eigh against
 scipy.linalg.expm.
 """

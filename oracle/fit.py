@@ -6,7 +6,7 @@ The paper applies the MPO to the MPS and fits the product back into an MPS of
 fixed bond dimension by minimising the 2-norm difference with a DMRG-like
 sweeping scheme (Sec. 2.2 and Table 1, "(i)DMRG" row, cost O(w D^3)); in its
 benchmark every time step is one such variational fit at fixed bond dimension
-(Sec. 7.2). The paper does not spell out the sweep, so the following reading is
+(Sec. 8.2). The paper does not spell out the sweep, so the following reading is
 fixed here and shared, as a written specification, with the GPU path:
 
   * bonds D_i = min(D, d^i, d^(L-i)); a product state sits in index 0 of every

@@ -20,7 +20,7 @@ Readings of the paper taken here:
     of the appendix entry by entry).
   * "Sort the 1's (3's) to the front" in Algorithm 2 is a stable partition: the
     relative order of the other entries is kept (a full sort contradicts the
-    bond-dimension table of Sec. 7.3 at N = 3).
+    bond-dimension table of Sec. 8.3 at N = 3).
   * Algorithm 4 removes the levels with no 1 and at least one 3; its factor uses
     the number of 3s.
   * Pipeline order: H^N -> Alg. 3 -> Alg. 1 -> Alg. 2 -> Alg. 4.

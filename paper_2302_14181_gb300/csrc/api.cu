@@ -123,6 +123,7 @@ struct tevo_mps_s {
   std::vector<size_t> env_off;
   Buf env, X, T, Bq, V, tau, beta, Atmp, Rm, gemm_ws, red;
   Buf qrflags;        // [0] error flag of the cooperative QR, [1..] reflector flags
+  Buf qrwy;           // Gram matrices and triangular factors of the WY blocks (Q formation)
   int qr_epoch = 0;
   bool coop_qr = true;  // off while a batched step issues (concurrent streams, graph capture)
   int oz_slices = 0;    // > 0 while a step runs its fp64 contractions as Ozaki-scheme GEMMs
@@ -237,7 +238,7 @@ int qr_q(tevo_mps s, int m, int n, bool keep_r) {
     e = qr64_factor(L, zp(s->Bq), m, n, zp(s->V), zp(s->tau), zp(s->beta), static_cast<double*>(s->red.p));
   TRY(e);
   if (keep_r) TRY(qr64_extract_r(L, zp(s->Bq), zp(s->beta), m, n, zp(s->Rm)));
-  return qr64_form_q(L, zp(s->V), zp(s->tau), m, n, zp(s->Bq), 1, m);
+  return qr64_form_q(L, zp(s->V), zp(s->tau), m, n, zp(s->Bq), 1, m, s->qrwy.p);
 }
 
 // store a column-major (Dl d) x Dr matrix as the site tensor [Dl][d][Dr]
@@ -288,6 +289,7 @@ int workspace(tevo_mps s, tevo_mpo W) {
   TRY(ensure(c, s->Rm, sizeof(z64) * (size_t)s->D * s->D + 64));
   TRY(ensure(c, s->gemm_ws, (size_t)48 << 20));
   TRY(ensure(c, s->red, sizeof(double) * 4096));
+  TRY(ensure(c, s->qrwy, qr64_wy_bytes(s->D * d)));
   if (!s->qrflags.p) {
     TRY(ensure(c, s->qrflags, sizeof(int) * ((size_t)s->D * d + 64)));
     TRYCUDA(cudaMemsetAsync(s->qrflags.p, 0, s->qrflags.bytes, c->stream));
@@ -750,7 +752,7 @@ extern "C" int mps_destroy(tevo_mps s) {
   for (auto& b : s->A) dfree(c, b);
   for (auto& b : s->Anew) dfree(c, b);
   for (Buf* b : {&s->scalars, &s->env, &s->X, &s->T, &s->Bq, &s->V, &s->tau, &s->beta, &s->Atmp, &s->Rm,
-                 &s->gemm_ws, &s->red, &s->qrflags, &s->oz_ws})
+                 &s->gemm_ws, &s->red, &s->qrflags, &s->qrwy, &s->oz_ws})
     dfree(c, *b);
   mixed_state_destroy(c, s->mixed);
   delete s;

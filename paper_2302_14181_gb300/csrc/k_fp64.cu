@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <cstdio>
 
@@ -472,28 +473,109 @@ __global__ void qr_step_kernel(double2* A, int m, int n, int k, double2* V, doub
   }
 }
 
-// Q column c = H_0 H_1 ... H_c e_c, one CTA per column; q kept in shared memory
-__global__ void qr_form_q_kernel(const double2* V, const double2* tau, int m, int n, double2* Q,
-                                 long long sQr, long long sQc, int heavy) {
+// ---------------------------------------------------------------------------
+// Explicit thin Q from the compact WY form of blocks of reflectors
+// (Schreiber - Van Loan): H_j0 H_j0+1 ... H_j1-1 = I - V_b T_b V_b^H with T_b
+// upper triangular, T[i][i] = tau_i and T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i],
+// G = V_b^H V_b. Column c of Q is the product of the blocks b = c / WY_NB ... 0
+// applied, last block first, to e_c, so that each block costs one reduction
+// round (WY_NB dot products together) instead of WY_NB dependent ones.
+// ---------------------------------------------------------------------------
+constexpr int WY_NB = 16;
+constexpr int WY_GRAM_SPLIT = 8;  // CTAs sharing the dot products of one block
+
+// G[b][i][j] = v_{j0+i}^H v_{j0+j} for i < j within block b (row >= j0 + j,
+// where v_{j0+j} starts); CTA (b, s) takes the pairs p = s, s + SPLIT, ...
+// one warp per pair
+__global__ void qr_wy_gram_kernel(const double2* V, int m, int n, double2* G) {
+  const int b = blockIdx.x, j0 = b * WY_NB, nbk = min(WY_NB, n - j0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int npair = nbk * (nbk - 1) / 2;
+  for (int p = blockIdx.y + WY_GRAM_SPLIT * warp; p < npair; p += WY_GRAM_SPLIT * nw) {
+    // p -> (i, j), i < j, row-major over the strict upper triangle
+    int i = 0, rem = p;
+    while (rem >= nbk - 1 - i) {
+      rem -= nbk - 1 - i;
+      ++i;
+    }
+    const int j = i + 1 + rem;
+    const double2* vi = V + (long long)(j0 + i) * m;
+    const double2* vj = V + (long long)(j0 + j) * m;
+    double2 sum = make_double2(0.0, 0.0);
+    for (int r = j0 + j + lane; r < m; r += 32) sum = cfma(cconj(vi[r]), vj[r], sum);
+    sum = warp_csum0(sum);
+    if (lane == 0) G[((size_t)b * WY_NB + i) * WY_NB + j] = sum;
+  }
+}
+
+// T_b from G_b and tau (one warp per block): column i of T is formed after
+// columns 0..i-1; lane r < i forms T[r][i]
+__global__ void qr_wy_t_kernel(const double2* tau, int n, const double2* G, double2* Tf) {
+  __shared__ double2 T[WY_NB][WY_NB];
+  const int b = blockIdx.x, j0 = b * WY_NB, nbk = min(WY_NB, n - j0);
+  const int lane = threadIdx.x;
+  const double2* Gb = G + (size_t)b * WY_NB * WY_NB;
+  for (int i = 0; i < nbk; ++i) {
+    const double2 ti = tau[j0 + i];
+    double2 t = make_double2(0.0, 0.0);
+    if (lane < i) {
+      // sum_{k = lane}^{i-1} T[lane][k] G[k][i] (T upper triangular)
+      for (int k = lane; k < i; ++k) t = cfma(T[lane][k], Gb[k * WY_NB + i], t);
+      t = cmul(make_double2(-ti.x, -ti.y), t);
+    } else if (lane == i) {
+      t = ti;
+    }
+    __syncwarp();
+    if (lane < WY_NB) T[lane][i] = lane <= i ? t : make_double2(0.0, 0.0);
+    __syncwarp();
+  }
+  for (int e = lane; e < WY_NB * WY_NB; e += 32) {
+    const int r = e / WY_NB, c = e % WY_NB;
+    Tf[(size_t)b * WY_NB * WY_NB + e] = (r < nbk && c < nbk) ? T[r][c] : make_double2(0.0, 0.0);
+  }
+}
+
+// column c of Q (one CTA per column; the first `heavy` blocks take the most
+// expensive columns and the rest the cheapest ones, so that blocks sharing a
+// multiprocessor pair a long column with a short one): q = e_c, then for b = c / WY_NB down to 0:
+// w = V_b^H q (warp i takes the dot products of reflectors i, i + nw, ...),
+// w' = T_b w, q -= V_b w'. Within block c / WY_NB only the reflectors up to c
+// act on e_c.
+__global__ void qr_wy_form_kernel(const double2* V, int m, int n, const double2* Tf, double2* Q, long long sQr,
+                                  long long sQc, int heavy) {
   extern __shared__ double2 q[];
-  __shared__ double red[64];
-  // column c costs c + 1 reflector applications: the first `heavy` blocks take
-  // the most expensive columns and the rest the cheapest ones, so that blocks
-  // sharing a multiprocessor pair a long column with a short one
+  __shared__ double2 w[WY_NB], wp[WY_NB];
   const int c = (int)blockIdx.x < heavy ? n - 1 - (int)blockIdx.x : (int)blockIdx.x - heavy;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int r = threadIdx.x; r < m; r += blockDim.x) q[r] = make_double2(r == c ? 1.0 : 0.0, 0.0);
   __syncthreads();
-  for (int k = c; k >= 0; --k) {
-    const double2 t = tau[k];
-    if (t.x == 0.0 && t.y == 0.0) continue;  // uniform across the block
-    const double2* vk = V + (long long)k * m;
-    double2 w = make_double2(0.0, 0.0);
-    for (int r = k + threadIdx.x; r < m; r += blockDim.x) w = cfma(cconj(vk[r]), q[r], w);
-    w = block_csum_every(w, red);
-    const double2 f = cmul(t, w);
-    for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
-      double2 d = cmul(vk[r], f);
-      q[r] = make_double2(q[r].x - d.x, q[r].y - d.y);
+  for (int b = c / WY_NB; b >= 0; --b) {
+    const int j0 = b * WY_NB;
+    const int nb = b == c / WY_NB ? c - j0 + 1 : min(WY_NB, n - j0);
+    for (int i = warp; i < nb; i += nw) {
+      const double2* vi = V + (long long)(j0 + i) * m;
+      double2 sum = make_double2(0.0, 0.0);
+      for (int r = j0 + i + lane; r < m; r += 32) sum = cfma(cconj(vi[r]), q[r], sum);
+      sum = warp_csum0(sum);
+      if (lane == 0) w[i] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) {
+      const double2* Tb = Tf + (size_t)b * WY_NB * WY_NB + (size_t)threadIdx.x * WY_NB;
+      double2 t = make_double2(0.0, 0.0);
+      for (int k = threadIdx.x; k < nb; ++k) t = cfma(Tb[k], w[k], t);
+      wp[threadIdx.x] = t;
+    }
+    __syncthreads();
+    for (int r = j0 + threadIdx.x; r < m; r += blockDim.x) {
+      double2 acc = q[r];
+      const int imax = min(nb, r - j0 + 1);  // v_{j0+i} is zero above row j0 + i
+      for (int i = 0; i < imax; ++i) {
+        const double2 d = cmul(V[(long long)(j0 + i) * m + r], wp[i]);
+        acc.x -= d.x;
+        acc.y -= d.y;
+      }
+      q[r] = acc;
     }
     __syncthreads();
   }
@@ -764,16 +846,15 @@ int qr64_factor(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_, z64*
   double2* beta = reinterpret_cast<double2*>(beta_);
   double* part = reinterpret_cast<double*>(scratch);
   double* frob2 = part + FROB_BLOCKS;
-  const double qflops = 8.0 * (4.0 * (double)m * n * n - 4.0 / 3.0 * (double)n * n * n);
+  const double qflops = 8.0 * ((double)m * n * n - (double)n * n * n / 3.0);
   int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_QR, qflops, 32.0 * (double)m * n) : -1;
   frob_partial_kernel<<<FROB_BLOCKS, 256, 0, L.stream>>>(A, (long long)m * n, part);
   sum_partials_kernel<<<1, 256, 0, L.stream>>>(part, FROB_BLOCKS, frob2);
   *L.launches += 2;
   const size_t smem = sizeof(double2) * (size_t)m;
   if (smem > 48 * 1024) {
-    static std::atomic<unsigned long long> attr_step{0}, attr_q{0};
-    if (smem_attr_once(qr_step_kernel, 200 * 1024, attr_step) || smem_attr_once(qr_form_q_kernel, 200 * 1024, attr_q))
-      return TEVO_ECUDA;
+    static std::atomic<unsigned long long> attr_step{0};
+    if (smem_attr_once(qr_step_kernel, 200 * 1024, attr_step)) return TEVO_ECUDA;
   }
   for (int k = 0; k < n; ++k) {
     int grid = n - k - 1;
@@ -802,7 +883,7 @@ int qr64_factor_coop(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_,
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_coop_kernel, 256, smem) != cudaSuccess ||
       per_sm * L.num_sms < G)
     return TEVO_EUNSUPPORTED;
-  const double qflops = 8.0 * (4.0 * (double)m * n * n - 4.0 / 3.0 * (double)n * n * n);
+  const double qflops = 8.0 * ((double)m * n * n - (double)n * n * n / 3.0);
   int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_QR, qflops, 32.0 * (double)m * n) : -1;
   frob_partial_kernel<<<FROB_BLOCKS, 256, 0, L.stream>>>(A, (long long)m * n, part);
   sum_partials_kernel<<<1, 256, 0, L.stream>>>(part, FROB_BLOCKS, frob2);
@@ -817,19 +898,32 @@ int qr64_factor_coop(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_,
   return e == cudaSuccess ? 0 : TEVO_ECUDA;
 }
 
-int qr64_form_q(const Launch& L, const z64* V, const z64* tau, int m, int n, z64* Q, long long sQr,
-                long long sQc) {
+size_t qr64_wy_bytes(int n) {
+  const size_t nblk = (size_t)(n + WY_NB - 1) / WY_NB;
+  return 2 * nblk * WY_NB * WY_NB * sizeof(double2);
+}
+
+int qr64_form_q(const Launch& L, const z64* V_, const z64* tau_, int m, int n, z64* Q, long long sQr, long long sQc,
+                void* wy) {
+  if (m < n || n <= 0) return TEVO_ESHAPE;
   const size_t smem = sizeof(double2) * (size_t)m;
   if (smem > 200 * 1024) return TEVO_EUNSUPPORTED;
   static std::atomic<unsigned long long> attr{0};
-  if (smem > 48 * 1024 && smem_attr_once(qr_form_q_kernel, 200 * 1024, attr)) return TEVO_ECUDA;
-  const double fflops = 8.0 * (4.0 * (double)m * n * n - 4.0 / 3.0 * (double)n * n * n) / 2.0;
+  if (smem > 48 * 1024 && smem_attr_once(qr_wy_form_kernel, 200 * 1024, attr)) return TEVO_ECUDA;
+  const double2* V = reinterpret_cast<const double2*>(V_);
+  const double2* tau = reinterpret_cast<const double2*>(tau_);
+  const int nblk = (n + WY_NB - 1) / WY_NB;
+  double2* G = static_cast<double2*>(wy);
+  double2* Tf = G + (size_t)nblk * WY_NB * WY_NB;
+  // complex Householder Q formation: 8 (m n^2 - n^3 / 3) flops
+  const double fflops = 8.0 * ((double)m * n * n - (double)n * n * n / 3.0);
   int pr = L.prof ? L.prof->begin(L.stream, TEVO_PROF_FORMQ, fflops, 32.0 * (double)m * n) : -1;
-  qr_form_q_kernel<<<n, QR_THREADS, smem, L.stream>>>(reinterpret_cast<const double2*>(V),
-                                                      reinterpret_cast<const double2*>(tau), m, n,
-                                                      reinterpret_cast<double2*>(Q), sQr, sQc,
-                                                      std::min(n, L.num_sms));
-  ++*L.launches;
+  if (nblk > 65535) return TEVO_ESHAPE;
+  qr_wy_gram_kernel<<<dim3(nblk, WY_GRAM_SPLIT), 256, 0, L.stream>>>(V, m, n, G);
+  qr_wy_t_kernel<<<nblk, 32, 0, L.stream>>>(tau, n, G, Tf);
+  qr_wy_form_kernel<<<n, 256, smem, L.stream>>>(V, m, n, Tf, reinterpret_cast<double2*>(Q), sQr, sQc,
+                                                std::min(n, L.num_sms));
+  *L.launches += 3;
   if (L.prof) L.prof->end(L.stream, pr);
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
 }

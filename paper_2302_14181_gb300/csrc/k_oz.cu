@@ -20,13 +20,15 @@
 // (all pairs of a group carry the weight 2^-(2P + W g)). One pass accumulates a
 // group over at most 2048 / (g + 1) K-indices: 2 (g + 1) K <= 4096 terms, so
 // the pass result is exact. The epilogue turns it into an integer and adds it,
-// shifted by its group's weight, to a 64-bit fixed-point sum per output entry;
-// after the last pass of a tile the sum is scaled by 2^(e_m + e_n) and rounded
+// shifted left by its group's weight, to one of two 64-bit fixed-point sums per
+// output entry (groups 0..3 and groups 4..7, the second in units 2^-28 of the
+// first), so the sums are exact; after the last pass of a tile the entry is
+// the exact 128-bit combination of the two, scaled by 2^(e_m + e_n) and rounded
 // once to fp64. The only errors are the dropped terms (digits past slice G-1
 // and pairs with s + t >= G), relative size about (G + 2) 2^-(W G) of
-// max|A_m.| max|B_n.| K (G = 8: 56 bits), the few bits of the last groups
-// below the fixed-point unit, and that final rounding. No per-pass work uses
-// the fp64 pipe, which on this part runs at about 1/1600 of the bf16 MMA rate.
+// max|A_m.| max|B_n.| K (G = 8: 56 bits), and that final rounding. No per-pass
+// work uses the fp64 pipe, which on this part runs at about 1/1600 of the bf16
+// MMA rate.
 //
 // The tensor-core schedule is that of the plain complex GEMM (k_tc.cu): a
 // persistent CTA per SM, a TMA producer warp, one thread issuing tcgen05.mma,
@@ -54,6 +56,12 @@ namespace {
 constexpr int OZ_P = 6;           // digits are integers in [-2^P, 2^P]
 constexpr int OZ_W = 7;           // weight ratio between consecutive slices: 2^W
 constexpr int OZ_MAX_SLICES = 8;  // (g + 1) * 256 <= 2048 keeps every pass below 2^24
+// pass values of groups 0..3 are summed in one 64-bit fixed-point accumulator,
+// those of groups 4..7 in a second one whose unit is 2^-28 of the first: every
+// pass value then enters its sum shifted left (never right), so both sums are
+// exact, and the entry is their exact 128-bit combination, rounded once
+constexpr int OZ_HI_GROUPS = 4;
+constexpr int OZ_LO_SHIFT = OZ_W * OZ_HI_GROUPS;
 constexpr int OZ_TM = 128, OZ_TN = 128;
 constexpr int OZ_KCB = 64;                 // bytes of K per stage row (32 bf16)
 constexpr int OZ_KT_CHUNK = 8;             // K-tiles of 32 per exact chunk: 256 K-indices
@@ -73,8 +81,8 @@ constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
 // one operand to cut into digit slices: element (r, k) of R x K at
 // src[(r / R2) * sR1 + (r % R2) * sR + k * sK] (conjugated when conj), digit
 // planes written to dst[p * plane_stride + r * row_pitch + k], the row maxima
-// of the magnitude bit patterns to maxbits[r] (zeroed before), the row
-// exponents to exps[r]
+// of the entries' exponent bounds to rowexp[r] (set to OZ_NONE before), the
+// row exponents to exps[r]
 struct OzSplit {
   const double2* src;
   long long sR, sK;
@@ -84,7 +92,7 @@ struct OzSplit {
   __nv_bfloat16* dst;
   long long plane_stride, row_pitch;
   int* exps;
-  unsigned long long* maxbits;
+  int* rowexp;
   int R2;
   long long sR1;
 };
@@ -103,7 +111,7 @@ struct OzArgs {
   int N2;
   long long sCn1;
   double2* part;  // [splits][M][N] when splits > 1
-  longlong2* acc;  // fixed-point sums: [CTA][column][row] of one 128 x 128 tile per CTA
+  longlong2* acc;  // fixed-point sums: [CTA][2][column][row], two sums of one 128 x 128 tile per CTA
   int base_shift;  // S unit: 2^-base_shift of a group-0 pass value
   int* err;
 };
@@ -120,21 +128,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
 // row exponent marking a row that holds a NaN or an infinity: its digits are
 // zero and every output entry it touches is NaN
 constexpr int OZ_NONFINITE = 0x7fff0000;
+// "no entry yet" of the exponent maxima (the byte pattern 0x80 repeated, so a
+// memset initialises it); far below any exponent of a finite double
+constexpr int OZ_NONE = (int)0x80808080;
 
-// exponent e with |x| < 2^e for the largest magnitude of a row, given the bit
-// pattern of that magnitude (0 for a zero row). Non-negative doubles order like
-// their bit patterns, so the row maximum is taken on integers.
-__device__ __forceinline__ int row_exponent_bits(unsigned long long mx) {
-  if (mx == 0) return 0;
-  const int E = (int)(mx >> 52);  // sign bit already cleared
-  if (E == 0x7FF) return OZ_NONFINITE;
-  return E == 0 ? -1022 : E - 1022;
-}
-
-__device__ __forceinline__ unsigned long long mag_bits(double2 v) {
+// exponent e with |v| < 2^e for the larger of |Re v|, |Im v| (from the binary64
+// fields): OZ_NONE for zero, OZ_NONFINITE for a NaN or an infinity
+__device__ __forceinline__ int exp_bound(double2 v) {
   const unsigned long long ax = (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull;
   const unsigned long long ay = (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull;
-  return ax > ay ? ax : ay;
+  const unsigned long long mx = ax > ay ? ax : ay;
+  if (mx == 0) return OZ_NONE;
+  const int E = (int)(mx >> 52);
+  if (E == 0x7FF) return OZ_NONFINITE;
+  return E == 0 ? -1022 : E - 1022;
 }
 
 // x * 2^(F - e) rounded to the nearest integer (ties to even), for |x| < 2^e:
@@ -203,7 +210,80 @@ __host__ __device__ double fixed_to_f64(long long s, int e2) {
 #endif
 }
 
-// row maxima of the magnitude bit patterns: a warp reduces one row over a
+// (hi 2^64 + lo) * 2^e2 for a two's-complement 128-bit integer, rounded to the
+// nearest fp64 (ties to even) from its leading 64 bits and a sticky bit for the
+// rest; results outside the normal range take an exact power-of-two scaling of
+// the rounded 53-bit significand
+#ifdef __CUDA_ARCH__
+__noinline__
+#endif
+__host__ __device__ double fixed128_to_f64(long long hi, unsigned long long lo, int e2) {
+  const bool neg = hi < 0;
+  unsigned long long uh = (unsigned long long)hi, ul = lo;
+  if (neg) {
+    ul = ~ul + 1ull;
+    uh = ~uh + (ul == 0 ? 1ull : 0ull);
+  }
+  if (uh == 0 && ul == 0) return 0.0;
+  int sh = 0;  // bits of the magnitude below its leading 64
+  unsigned long long top = ul;
+  bool sticky = false;
+  if (uh != 0) {
+#ifdef __CUDA_ARCH__
+    sh = 64 - __clzll((long long)uh);
+#else
+    sh = 64 - __builtin_clzll(uh);
+#endif
+    top = sh == 64 ? uh : ((uh << (64 - sh)) | (ul >> sh));
+    sticky = sh == 64 ? (ul != 0) : ((ul & ((1ull << sh) - 1ull)) != 0);
+  }
+#ifdef __CUDA_ARCH__
+  const int nb = 64 - __clzll((long long)top);
+#else
+  const int nb = 64 - __builtin_clzll(top);
+#endif
+  unsigned long long q;
+  int exq = nb - 1 + sh + e2;  // exponent of the leading bit
+  if (nb <= 53) {
+    q = top << (53 - nb);  // exact (sticky is set only when nb == 64)
+  } else {
+    const int drop = nb - 53;
+    q = top >> drop;
+    const unsigned long long rem = top & ((1ull << drop) - 1ull), half = 1ull << (drop - 1);
+    if (rem > half || (rem == half && (sticky || (q & 1ull)))) {
+      ++q;
+      if (q >> 53) {
+        q >>= 1;
+        ++exq;
+      }
+    }
+  }
+  if (exq < -1022 || exq > 1023) {
+    const double r = ldexp((double)q, exq - 52);
+    return neg ? -r : r;
+  }
+  const unsigned long long bits = ((unsigned long long)neg << 63) | ((unsigned long long)(exq + 1023) << 52) |
+                                  (q & ((1ull << 52) - 1ull));
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)bits);
+#else
+  double d;
+  std::memcpy(&d, &bits, sizeof(d));
+  return d;
+#endif
+}
+
+// the exact value S0 2^OZ_LO_SHIFT + S1 of the two fixed-point sums, times 2^e2
+__device__ __forceinline__ double combine_to_f64(long long s0, long long s1, int e2) {
+  // s0 2^28 as 128 bits, then + s1 sign-extended
+  long long hi = s0 >> (64 - OZ_LO_SHIFT);
+  unsigned long long lo = (unsigned long long)s0 << OZ_LO_SHIFT;
+  const unsigned long long lo2 = lo + (unsigned long long)s1;
+  hi += (s1 >> 63) + (lo2 < lo ? 1 : 0);
+  return fixed128_to_f64(hi, lo2, e2);
+}
+
+// row maxima of the exponent bounds: a warp reduces one row over a
 // segment of 256 K-indices (K contiguous or general strides) and merges it
 // with atomicMax, so long rows are spread over many warps
 __global__ void oz_rowmax_warp_kernel(OzSplit o, int nseg) {
@@ -214,17 +294,11 @@ __global__ void oz_rowmax_warp_kernel(OzSplit o, int nseg) {
     const long long r = w / nseg;
     const int k0 = int(w % nseg) * 256;
     const double2* src = o.src + row_offset(o, r);
-    unsigned long long mx = 0;
-    for (int k = k0 + lane; k < min(o.K, k0 + 256); k += 32) {
-      const unsigned long long v = mag_bits(src[(long long)k * o.sK]);
-      mx = v > mx ? v : mx;
-    }
+    int mx = OZ_NONE;
+    for (int k = k0 + lane; k < min(o.K, k0 + 256); k += 32) mx = max(mx, exp_bound(src[(long long)k * o.sK]));
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, off);
-      mx = v > mx ? v : mx;
-    }
-    if (lane == 0 && mx) atomicMax(o.maxbits + r, mx);
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0 && mx != OZ_NONE) atomicMax(o.rowexp + r, mx);
   }
 }
 
@@ -240,12 +314,9 @@ __global__ void oz_rowmax_lane_kernel(OzSplit o, int nseg) {
     const int k0 = int(w % nseg) * 64;
     if (r >= o.R) continue;
     const double2* src = o.src + row_offset(o, r);
-    unsigned long long mx = 0;
-    for (int k = k0; k < min(o.K, k0 + 64); ++k) {
-      const unsigned long long v = mag_bits(src[(long long)k * o.sK]);
-      mx = v > mx ? v : mx;
-    }
-    if (mx) atomicMax(o.maxbits + r, mx);
+    int mx = OZ_NONE;
+    for (int k = k0; k < min(o.K, k0 + 64); ++k) mx = max(mx, exp_bound(src[(long long)k * o.sK]));
+    if (mx != OZ_NONE) atomicMax(o.rowexp + r, mx);
   }
 }
 
@@ -294,7 +365,8 @@ __global__ void oz_slice_kernel(OzSplit o) {
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int r = r0 + i, k = k0 + 2 * threadIdx.x;
     if (r >= o.R || k >= o.K) continue;
-    const int e = row_exponent_bits(o.maxbits[r]);
+    const int er = o.rowexp[r];
+    const int e = er == OZ_NONE ? 0 : er;  // a zero row
     if (k0 == 0 && threadIdx.x == 0) o.exps[r] = e;
     const bool fin = e != OZ_NONFINITE;
     // entries past K are zero (tile padding), so the pair never needs a tail case
@@ -480,17 +552,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
   } else {
     // epilogue: warps 2..9; warp w owns tensor-memory lane quarter w % 4 and half
-    // of the tile's columns. A pass
-    // value is an exact integer held in fp32; the passes of a unit are summed
-    // in a 64-bit fixed-point accumulator S with integer operations only. S
-    // lives in this CTA's slice of the workspace, laid out [column][row] so that
-    // a warp touches 32 consecutive rows, and is converted to fp64 once, after
-    // the unit's last pass.
+    // of the tile's columns. A pass value is an exact integer held in fp32; the
+    // passes of a unit are summed with integer operations only, groups 0..3 in
+    // the 64-bit fixed-point accumulator S0 and groups 4..7 in S1 (unit 2^-28 of
+    // S0's), both exact. They live in this CTA's slice of the workspace, laid
+    // out [column][row] so that a warp touches 32 consecutive rows, and the entry
+    // is converted to fp64 once, after the unit's last pass.
     const int qw = warp % 4;
     const int c_lo = ((warp - 2) / 4) * (OZ_TN * 4 / OZ_EPI_WARPS);  // this warp's columns
     const int c_hi = c_lo + OZ_TN * 4 / OZ_EPI_WARPS;
     const int row = qw * 32 + lane;
-    longlong2* S = a.acc + (size_t)blockIdx.x * OZ_TM * OZ_TN + row;
+    longlong2* S0 = a.acc + (size_t)blockIdx.x * 2 * OZ_TM * OZ_TN + row;
+    longlong2* S1 = S0 + OZ_TM * OZ_TN;
     int i = 0;
     bool ok = true;
     for (int u = cid; u < nunits && ok; u += ncl) {
@@ -508,9 +581,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const bool first = (g == 0 && p0 == t0), last = (g == a.G - 1 && p0 + pass_len(g) >= t1);
-          // weight of this group in S: 2^(base_shift - W g) units of the pass value
-          const int shift = a.base_shift - OZ_W * g;
+          const int h = g / OZ_HI_GROUPS;  // accumulator of this group
+          longlong2* S = h ? S1 : S0;
+          const bool first = (g == OZ_HI_GROUPS * h && p0 == t0), last = (g == a.G - 1 && p0 + pass_len(g) >= t1);
+          // weight of this group in its sum: 2^shift units of the pass value,
+          // shift = base_shift + 28 h - W g >= base_shift - 21 >= 0
+          const int shift = a.base_shift + OZ_LO_SHIFT * h - OZ_W * g;
           const uint32_t trow = tmem + (uint32_t)(b * 2 * OZ_TN) + ((uint32_t)(qw * 32) << 16);
           for (int cc = c_lo; cc < c_hi; cc += 16) {
             uint32_t rr[16], ri[16];
@@ -523,33 +599,39 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              const int col = cc + j;
-              long long vr = (long long)__float2int_rn(__uint_as_float(rr[j]));
-              long long vi = (long long)__float2int_rn(__uint_as_float(ri[j]));
-              vr = (shift >= 0 ? vr * (1LL << shift) : (vr >> -shift)) + old[j].x;
-              vi = (shift >= 0 ? vi * (1LL << shift) : (vi >> -shift)) + old[j].y;
-              if (!last) {
-                S[(size_t)col * OZ_TM] = make_longlong2(vr, vi);
-              } else if (m < a.M && n0 + col < a.N) {
-                const int n = n0 + col;
-                const int en = a.eb[n];
-                double2* dst = a.splits == 1 ? a.C + (long long)m * a.sCm + (long long)(n / a.N2) * a.sCn1 +
-                                                   (long long)(n % a.N2) * a.sCn
-                                             : a.part + ((long long)z * a.M + m) * (long long)a.N + n;
-                if (em == OZ_NONFINITE || en == OZ_NONFINITE) {
-                  *dst = make_double2(__longlong_as_double(0x7FF8000000000000LL),
-                                      __longlong_as_double(0x7FF8000000000000LL));
-                } else {
-                  const int e2 = em + en - 2 * OZ_P - a.base_shift;
-                  *dst = make_double2(fixed_to_f64(vr, e2), fixed_to_f64(vi, e2));
-                }
-              }
+              const long long vr = (long long)__float2int_rn(__uint_as_float(rr[j]));
+              const long long vi = (long long)__float2int_rn(__uint_as_float(ri[j]));
+              S[(size_t)(cc + j) * OZ_TM] = make_longlong2(vr * (1LL << shift) + old[j].x, vi * (1LL << shift) + old[j].y);
             }
           }
           // this warp is done reading the buffer: hand it back to the MMA warp
+          // (before the conversion below, which reads only the sums)
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+          if (last) {
+            // the unit's entries of this lane's row: exact sums to fp64, once
+            for (int col = c_lo; col < c_hi; ++col) {
+              const int n = n0 + col;
+              if (m >= a.M || n >= a.N) continue;
+              double2* dst = a.splits == 1 ? a.C + (long long)m * a.sCm + (long long)(n / a.N2) * a.sCn1 +
+                                                 (long long)(n % a.N2) * a.sCn
+                                           : a.part + ((long long)z * a.M + m) * (long long)a.N + n;
+              const int en = a.eb[n];
+              if (em == OZ_NONFINITE || en == OZ_NONFINITE) {
+                *dst = make_double2(__longlong_as_double(0x7FF8000000000000LL),
+                                    __longlong_as_double(0x7FF8000000000000LL));
+              } else if (h == 0) {
+                const longlong2 v = S0[(size_t)col * OZ_TM];
+                const int e2 = em + en - 2 * OZ_P - a.base_shift;
+                *dst = make_double2(fixed_to_f64(v.x, e2), fixed_to_f64(v.y, e2));
+              } else {
+                const longlong2 hi = S0[(size_t)col * OZ_TM], lo = S1[(size_t)col * OZ_TM];
+                const int e2 = em + en - 2 * OZ_P - a.base_shift - OZ_LO_SHIFT;
+                *dst = make_double2(combine_to_f64(hi.x, lo.x, e2), combine_to_f64(hi.y, lo.y, e2));
+              }
+            }
+          }
         }
     }
   }
@@ -589,12 +671,12 @@ OzPlan plan(int M, int N, int K, int G, int num_sms) {
   const long long kp = pad8(K);
   p.a_bytes = al256((size_t)2 * G * M * kp * 2);
   p.b_bytes = al256((size_t)2 * G * N * kp * 2);
-  p.e_bytes = al256((size_t)(M + N) * (sizeof(int) + sizeof(unsigned long long)));
+  p.e_bytes = al256((size_t)(M + N) * 2 * sizeof(int));
   p.p_bytes = p.splits > 1 ? al256((size_t)p.splits * M * N * 16) : 0;
   // persistent grid: one CTA per SM at most
   const long long units = (long long)((M + OZ_TM - 1) / OZ_TM) * ((N + OZ_TN - 1) / OZ_TN) * p.splits;
   p.grid = (int)std::max<long long>(1, std::min<long long>(units, (long long)num_sms));
-  p.s_bytes = al256((size_t)p.grid * OZ_TM * OZ_TN * sizeof(longlong2));
+  p.s_bytes = al256((size_t)p.grid * 2 * OZ_TM * OZ_TN * sizeof(longlong2));
   // |pass value| <= 2^24 and sum_g 2^-W g < 1.008: cps chunks stay below
   // 2^(base_shift + 24 + log2 cps + 0.02) <= 2^62.02 < 2^63
   int lg = 0;
@@ -604,8 +686,7 @@ OzPlan plan(int M, int N, int K, int G, int num_sms) {
 }
 
 int split_operand(const Launch& L, const OzSplit& o) {
-  if (cudaMemsetAsync(o.maxbits, 0, sizeof(unsigned long long) * (size_t)o.R, L.stream) != cudaSuccess)
-    return TEVO_ECUDA;
+  if (cudaMemsetAsync(o.rowexp, 0x80, sizeof(int) * (size_t)o.R, L.stream) != cudaSuccess) return TEVO_ECUDA;
   const bool rows_contig = o.sR == 1 && o.sK != 1;
   if (rows_contig) {
     const int nseg = (o.K + 63) / 64;
@@ -647,7 +728,7 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
   const int Nt = (int)total_n(g);
   if (slices < 1 || slices > OZ_MAX_SLICES) return TEVO_EINVAL;
   if (g.M <= 0 || g.N <= 0) return 0;
-  if (g.K <= 0) return TEVO_EUNSUPPORTED;
+  if (g.K <= 0 || g.K > (1 << 25)) return TEVO_EUNSUPPORTED;  // keeps every accumulator shift >= 0
   static std::atomic<unsigned long long> attr_done{0};
   if (smem_attr_once(oz_gemm_kernel, OZ_SMEM_BYTES, attr_done)) return TEVO_ECUDA;
   const OzPlan p = plan(g.M, Nt, g.K, slices, L.num_sms);
@@ -657,9 +738,9 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
   w += p.a_bytes;
   __nv_bfloat16* db = reinterpret_cast<__nv_bfloat16*>(w);
   w += p.b_bytes;
-  unsigned long long* mxa = reinterpret_cast<unsigned long long*>(w);
-  unsigned long long* mxb = mxa + g.M;
-  int* ea = reinterpret_cast<int*>(mxb + Nt);
+  int* mxa = reinterpret_cast<int*>(w);
+  int* mxb = mxa + g.M;
+  int* ea = mxb + Nt;
   int* eb = ea + g.M;
   w += p.e_bytes;
   double2* part = p.splits > 1 ? reinterpret_cast<double2*>(w) : nullptr;

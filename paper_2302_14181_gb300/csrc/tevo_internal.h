@@ -121,9 +121,12 @@ int qr64_factor(const Launch& L, z64* A, int m, int n, z64* V, z64* tau, z64* be
 // TEVO_EUNSUPPORTED when the matrix does not fit (then use qr64_factor)
 int qr64_factor_coop(const Launch& L, z64* A, int m, int n, z64* V, z64* tau, z64* beta, void* scratch, int* flags,
                      int epoch, int* err);
-// explicit thin Q (m x n) written with element (r, c) at Q[r * sQr + c * sQc]
+// explicit thin Q (m x n) written with element (r, c) at Q[r * sQr + c * sQc],
+// from the compact WY form of blocks of reflectors; wy: qr64_wy_bytes(n) bytes
+// of device workspace (the blocks' Gram matrices and triangular factors)
+size_t qr64_wy_bytes(int n);
 int qr64_form_q(const Launch& L, const z64* V, const z64* tau, int m, int n, z64* Q, long long sQr,
-                long long sQc);
+                long long sQc, void* wy);
 // R (n x n) from the factored A and beta: dense upper-triangular, row-major
 int qr64_extract_r(const Launch& L, const z64* A, const z64* beta, int m, int n, z64* R);
 

@@ -30,12 +30,18 @@ def ops_for(d):
     return list(wl.pauli()) if d == 2 else list(wl.spin_one())
 
 
-def run(name, steps=None, record=None, tag=None, **override):
+def run(name, steps=None, record=None, tag=None, last_tau=None, **override):
+    """Oracle evolution of a named workload; with last_tau the final step uses
+    an MPO built at that time step (a total time that is not a multiple of tau:
+    e.g. 12 steps of 0.4 and one of 0.2 reach t = 5)."""
     cfg = wl.config(name, **override)
     if steps is not None:
         cfg["steps"] = steps
     A, B, C, D = wl.model_blocks(cfg)
     W = mpo.build_mpo(A, B, C, D, cfg["N"], cfg["tau"])
+    W_last = mpo.build_mpo(A, B, C, D, cfg["N"], last_tau) if last_tau is not None else W
+    if last_tau is not None:
+        cfg["last_tau"] = last_tau
     psi = fit.product_mps(wl.initial_vectors(cfg), cfg["D"])
     ops = ops_for(cfg["d"])
     record = set(record or range(1, cfg["steps"] + 1))
@@ -47,7 +53,8 @@ def run(name, steps=None, record=None, tag=None, **override):
     logn = 0.0
     t0 = time.time()
     for k in range(1, cfg["steps"] + 1):
-        psi, ln = fit.evolve_step(psi, W, cfg["sweeps"], canonical=(k > 1))
+        Wk = W_last if k == cfg["steps"] else W
+        psi, ln = fit.evolve_step(psi, Wk, cfg["sweeps"], canonical=(k > 1))
         logn += ln
         out["log_norm"].append(logn)
         if k in record:
@@ -69,6 +76,8 @@ if __name__ == "__main__":
     ap.add_argument("--D", type=int)
     ap.add_argument("--tau", type=float, help="imaginary part magnitude: tau = -i*value")
     ap.add_argument("--tag", type=str)
+    ap.add_argument("--last-tau", type=float, help="time step of the final step: tau = -i*value")
+    ap.add_argument("--sweeps", type=int)
     a = ap.parse_args()
     ov = {}
     if a.L:
@@ -77,5 +86,8 @@ if __name__ == "__main__":
         ov["D"] = a.D
     if a.tau:
         ov["tau"] = -1j * a.tau
+    if a.sweeps:
+        ov["sweeps"] = a.sweeps
     rec = [int(x) for x in a.record.split(",")] if a.record else None
-    run(a.workload, steps=a.steps, record=rec, tag=a.tag, **ov)
+    run(a.workload, steps=a.steps, record=rec, tag=a.tag,
+        last_tau=(-1j * a.last_tau) if a.last_tau else None, **ov)

@@ -10,10 +10,10 @@ imaginary parts, and their G balanced base-2^W digits. Per output tile the
 K-range is cut as the kernel plans it (K-tiles of 32 in chunks of 8; split-K
 over chunks when there are fewer tiles than SMs); per group g = s + t the
 digit products are summed exactly over passes of at most 64 / (g + 1) K-tiles,
-each pass value is shifted by (base_shift - W g) bits (an arithmetic right
-shift when negative) into a 64-bit fixed-point sum, and the sum is rounded
-once to fp64. Split partials are added in fp64 in split order, starting from
-0.0.
+each pass value is shifted left by (base_shift + 28 h - W g) bits into the
+64-bit fixed-point sum h = g // 4 (groups 0..3 and 4..7), both sums exact; the
+entry is the exact value S0 2^28 + S1, rounded once to fp64. Split partials
+are added in fp64 in split order, starting from 0.0.
 """
 from __future__ import annotations
 
@@ -26,23 +26,42 @@ TM = TN = 128          # output tile of one CTA
 KT = 32                # K-indices per K-tile
 CHUNK = 8              # K-tiles per exact chunk
 NONFINITE = None
+HI_GROUPS = 4          # groups 0..3 in the first fixed-point sum, 4..7 in the second
+LO_SHIFT = W * HI_GROUPS
+
+
+def exp_bound(z):
+    """e with max(|Re z|, |Im z|) < 2^e from the binary64 fields of the larger
+    magnitude: biased exponent E -> E - 1022 (normal), -1022 (subnormal); None
+    for zero, NONFINITE_E for a NaN or an infinity."""
+    mag = max(abs(z.real), abs(z.imag))
+    if mag == 0.0:
+        return None
+    if not math.isfinite(mag):
+        return NONFINITE_E
+    E = int(np.float64(mag).view(np.uint64)) >> 52
+    return -1022 if E == 0 else E - 1022
+
+
+NONFINITE_E = "nonfinite"
 
 
 def row_exponents(X):
-    """e_r from the bit pattern of max(|Re|, |Im|) over row r: biased exponent
-    E -> E - 1022 (normal), -1022 (subnormal), 0 (zero row), None (NaN / Inf)."""
-    mag = np.maximum(np.abs(X.real), np.abs(X.imag))
-    bits = mag.view(np.uint64) if mag.dtype == np.float64 else mag.astype(np.float64).view(np.uint64)
+    """e_r: the largest exponent bound over row r; 0 for a zero row, None
+    (NONFINITE) when the row holds a NaN or an infinity."""
+    R, K = X.shape
     out = []
-    for row in bits:
-        mx = int(row.max()) if row.size else 0
-        E = mx >> 52
-        if mx == 0:
-            out.append(0)
-        elif E == 0x7FF:
-            out.append(NONFINITE)
-        else:
-            out.append(-1022 if E == 0 else E - 1022)
+    for r in range(R):
+        best, bad = None, False
+        for k in range(K):
+            e = exp_bound(X[r, k])
+            if e is None:
+                continue
+            if e == NONFINITE_E:
+                bad = True
+                continue
+            best = e if best is None else max(best, e)
+        out.append(NONFINITE if bad else (0 if best is None else best))
     return out
 
 
@@ -125,11 +144,13 @@ def gemm(A, B, G=8, num_sms=152):
     for z in range(splits):
         t0 = z * cps * CHUNK
         t1 = min(k_tiles, (z + 1) * cps * CHUNK)
-        S_re = np.zeros((M, N), np.int64)
-        S_im = np.zeros((M, N), np.int64)
+        S_re = np.zeros((2, M, N), np.int64)
+        S_im = np.zeros((2, M, N), np.int64)
         for g in range(G):
             plen = 64 // (g + 1)
-            shift = base_shift - W * g
+            h = g // HI_GROUPS
+            shift = base_shift + LO_SHIFT * h - W * g
+            assert shift >= 0
             for p0 in range(t0, t1, plen):
                 k0, k1 = p0 * KT, min(t1, p0 + plen) * KT
                 v_re = np.zeros((M, N), np.int64)
@@ -141,20 +162,19 @@ def gemm(A, B, G=8, num_sms=152):
                     v_re += a_r @ b_r.T - a_i @ b_i.T
                     v_im += a_r @ b_i.T + a_i @ b_r.T
                 assert np.abs(v_re).max(initial=0) < 2 ** 24 and np.abs(v_im).max(initial=0) < 2 ** 24
-                if shift >= 0:
-                    S_re += v_re << shift
-                    S_im += v_im << shift
-                else:
-                    S_re += v_re >> -shift
-                    S_im += v_im >> -shift
+                S_re[h] += v_re << shift
+                S_im[h] += v_im << shift
+                assert np.abs(S_re[h]).max(initial=0) < 2 ** 63 and np.abs(S_im[h]).max(initial=0) < 2 ** 63
         part = np.empty((M, N), np.complex128)
         for m in range(M):
             for n in range(N):
                 if ea[m] is NONFINITE or eb[n] is NONFINITE:
                     part[m, n] = complex(math.nan, math.nan)
                     continue
-                e2 = ea[m] + eb[n] - 2 * P - base_shift
-                part[m, n] = complex(_scaled(int(S_re[m, n]), e2), _scaled(int(S_im[m, n]), e2))
+                e2 = ea[m] + eb[n] - 2 * P - base_shift - LO_SHIFT
+                tot_re = (int(S_re[0, m, n]) << LO_SHIFT) + int(S_re[1, m, n])
+                tot_im = (int(S_im[0, m, n]) << LO_SHIFT) + int(S_im[1, m, n])
+                part[m, n] = complex(_scaled(tot_re, e2), _scaled(tot_im, e2))
         partials.append(part)
     if splits == 1:
         return partials[0]
@@ -166,7 +186,8 @@ def gemm(A, B, G=8, num_sms=152):
 
 
 def _scaled(s, e2):
-    """s 2^e2 rounded to fp64 (s an integer below 2^63 in magnitude)."""
+    """s 2^e2 rounded to fp64 (s an integer; float() rounds it to nearest, ties
+    to even)."""
     try:
         return math.ldexp(float(s), e2)
     except OverflowError:

@@ -1,5 +1,5 @@
 """Uses of evolve_step beyond real-time steps with one MPO: complex-step
-splitting (Sec. 7.3) and real tau (imaginary time, towards the ground state)."""
+splitting (Sec. 8.3) and real tau (imaginary time, towards the ground state)."""
 import numpy as np
 import pytest
 

@@ -105,18 +105,54 @@ def test_non_canonical_start(ctx):
         assert rel_err(tv.measure_local(psi, ops).real, fit.measure_local(psi_o, ops).real) < FP64_TOL
 
 
+def assert_equal_up_to_bond_phases(got, ref, tol):
+    """got_i = conj(P_i) ref_i P_(i+1) for diagonal phase matrices P_i on the
+    bonds (the gauge freedom that leaves the state unchanged: a Householder
+    column whose leading entry is zero in exact arithmetic takes its sign from
+    rounding). The phases of bond i+1 are fitted column by column from site i,
+    given those of bond i; the outer bonds carry the state's global phase."""
+    p = np.ones(1, complex)
+    for i, (a, b) in enumerate(zip(got, ref)):
+        bl = np.conj(p)[:, None, None] * b
+        c = np.einsum("lsr,lsr->r", np.conj(bl), a)
+        q = np.where(np.abs(c) > 0, c / np.where(np.abs(c) > 0, np.abs(c), 1), 1)
+        assert np.abs(a - bl * q[None, None, :]).max() < tol, i
+        p = q
+
+
 def test_tensors_right_canonical_and_close(ctx):
     """After a step the stored tensors are right-canonical (sites 2..L) and equal
-    the oracle's tensors up to rounding (same Householder convention)."""
+    the oracle's tensors up to rounding (same Householder convention) and up to
+    the phases of reflections whose sign rounding decides (a product-state
+    start has exact zeros there)."""
     L, D = 10, 8
     blocks = wl.xxz_blocks(L, 0.5)
     _, _, _, psi, psi_o = run_both(ctx, blocks, wl.product_state("neel", L), 2, -0.2j, D, 2, 1)
+    got = [psi.site(i) for i in range(L)]
+    for i in range(1, L):
+        G = np.einsum("asb,csb->ac", got[i], got[i].conj())
+        assert np.abs(G - np.eye(got[i].shape[0])).max() < 1e-12
+    assert_equal_up_to_bond_phases(got, psi_o, 1e-9)
+
+
+def test_tensors_equal_the_oracle_from_a_generic_state(ctx):
+    """From a random (entangled, full-rank) state every Householder sign is
+    decided by a nonzero leading entry: after a step the tensors equal the
+    oracle's up to rounding, with no phase freedom left."""
+    L, D = 10, 8
+    blocks = wl.xxz_blocks(L, 0.5)
+    A = wl.random_mps(L, 2, D, seed=77)
+    Wo = mpo.build_mpo(*blocks, 2, -0.2j)
+    W = tv.mpo_build(ctx, *blocks, 2, -0.2j)
+    psi = tv.mps_init(ctx, np.ones((L, 2)) / np.sqrt(2), D)
     for i in range(L):
-        a = psi.site(i)
-        if i > 0:
-            G = np.einsum("asb,csb->ac", a, a.conj())
-            assert np.abs(G - np.eye(a.shape[0])).max() < 1e-12
-        assert np.abs(a - psi_o[i]).max() < 1e-9
+        psi.set_site(i, A[i])
+    psi_o = A
+    for k in range(2):
+        psi_o, _ = fit.evolve_step(psi_o, Wo, 2, canonical=k > 0)
+        tv.evolve_step(psi, W, -0.2j, D, 2, tv.FP64)
+    for i in range(L):
+        assert np.abs(psi.site(i) - psi_o[i]).max() < 1e-9, i
 
 
 def test_measure_and_overlap_random_states(ctx):

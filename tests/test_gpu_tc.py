@@ -113,3 +113,28 @@ def test_bounded_wait_gives_up_and_context_survives(ctx):
     assert rc == -7 and code.value == 7
     A = np.ones((4, 3), np.complex128)
     assert np.allclose(tc_gemm(ctx, tv.BF16X3, A, A), A @ A.T)
+
+
+@pytest.mark.parametrize("prec,tol", [(tv.BF16X3 | tv.TC_ONLY, 2e-3), (tv.TF32X3 | tv.TC_ONLY, 2e-4)])
+def test_tensor_core_only_forms_against_oracle(ctx, prec, tol):
+    """Every sweep on the tensor cores (no fp64 sweep; fp64 QR and reductions):
+    the long-range Ising chain at L = 20, D = 24, N = 3, 4 steps of 2 sweeps,
+    against the fp64 oracle. The tolerance follows the split products' relative
+    error per contraction (bf16x3 about 2^-16, tf32x3 about 2^-22) times the
+    growth over the steps."""
+    L, D, N, tau = 20, 24, 3, -0.2j
+    blocks = wl.lr_ising_blocks(L, 0.7)
+    v0 = wl.product_state("up", L)
+    ops = list(wl.pauli())
+    Wo = mpo.build_mpo(*blocks, N, tau)
+    W = tv.mpo_build(ctx, *blocks, N, tau)
+    psi = tv.mps_init(ctx, v0, D)
+    psi_o = fit.product_mps(v0, D)
+    errs = []
+    for k in range(4):
+        psi_o, _ = fit.evolve_step(psi_o, Wo, 2, canonical=k > 0)
+        tv.evolve_step(psi, W, tau, D, 2, prec)
+        ref = fit.measure_local(psi_o, ops).real
+        errs.append(float(np.abs(tv.measure_local(psi, ops).real - ref).max() / max(np.abs(ref).max(), 1e-3)))
+    print("tc-only", hex(prec), [f"{e:.1e}" for e in errs])
+    assert max(errs) < tol, errs

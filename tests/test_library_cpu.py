@@ -72,7 +72,7 @@ def test_host_mpo_matches_oracle(model, N, variant):
 
 @pytest.mark.parametrize("chi,N", [(1, 4), (3, 4), (4, 3), (2, 5)])
 def test_host_mpo_bond_table(chi, N):
-    """Bond dimensions of the Sec. 7.3 table (and their N = 5 continuation
+    """Bond dimensions of the Sec. 8.3 table (and their N = 5 continuation
     computed by the oracle) from the C++ construction."""
     A, B, C, D = wl.random_blocks(3, chi, 1, seed=chi)
     Wc = tv.mpo_build_host(A, B, C, D, N, 0.1)

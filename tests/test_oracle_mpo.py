@@ -176,7 +176,7 @@ def test_appendix_second_order(scalar_blocks):
 
 @pytest.mark.parametrize("chi", [1, 2, 3, 4])
 def test_bond_dimension_table(chi):
-    """Sec. 7.3 table: w = 1+chi, 1+chi+chi^2, 1+3chi+chi^2+chi^3,
+    """Sec. 8.3 table: w = 1+chi, 1+chi+chi^2, 1+3chi+chi^2+chi^3,
     1+5chi+4chi^2+chi^3+chi^4 for N = 1..4 (full pipeline); after Algorithm 2
     alone the counts are 1+chi, 1+2chi+chi^2, 1+4chi+2chi^2+chi^3,
     1+6chi+5chi^2+2chi^3+chi^4 (same readings)."""
@@ -231,7 +231,7 @@ def test_exact_compression_is_exact(N, chi):
 
 @pytest.mark.parametrize("model", ["tfi", "xxz", "lri"])
 def test_error_order(model):
-    """Secs. 7.1-7.2: the order-N MPO approximates exp(tau H) with an error
+    """Secs. 8.1-8.2: the order-N MPO approximates exp(tau H) with an error
     O(tau^(N+1)); every variant keeps the order and the full pipeline is no less
     accurate than exact compression alone."""
     L = 6
@@ -254,7 +254,7 @@ def test_error_order(model):
 
 
 def test_full_pipeline_not_worse_than_exact_only():
-    """Sec. 7.1: the extended + approximately compressed MPO is more precise than
+    """Sec. 8.1: the extended + approximately compressed MPO is more precise than
     the exact-only one at equal tau (spin-1 Heisenberg chain)."""
     L = 5
     blocks = wl.spin1_blocks(L, 1.0, 0.3)
@@ -303,7 +303,7 @@ def test_site_dependent_couplings_match_dense():
 
 @pytest.mark.parametrize("variant", [mpo.FULL, mpo.PLAIN])
 def test_complex_step_splitting_is_second_order(variant):
-    """Sec. 7.3: two first-order operators at the complex steps tau (1 + i)/2 and
+    """Sec. 8.3: two first-order operators at the complex steps tau (1 + i)/2 and
     tau (1 - i)/2 compose to a second-order approximation of exp(tau H): the
     error falls by 2^3 when tau halves."""
     L = 6

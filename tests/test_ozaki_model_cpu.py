@@ -103,3 +103,4 @@ def test_digits_and_fixed_point_of_the_model():
     assert oz.to_fixed(1.0, 2, 1) == 0                       # 0.5 -> 0 (even)
     assert oz.to_fixed(3.0, 2, 1) == 2                       # 1.5 -> 2 (even)
     assert oz.to_fixed(-3.0, 2, 1) == -2
+

@@ -180,7 +180,7 @@ def random_mps(L, d, D, seed):
 
 
 # ----------------------------------------------------------------------------
-# named workloads (shapes of the paper's benchmark settings, Sec. 7)
+# named workloads (shapes of the paper's benchmark settings, Sec. 8)
 # ----------------------------------------------------------------------------
 
 CONFIGS = {
