@@ -3,13 +3,19 @@ fitted back to bond dimension D by variational sweeps, one step after another.
 
 One bench step = one call of evolve_step (all sweeps of one time step, with its
 environment build, QRs, centre and normalisation) on the long-range Ising chain
-L = 100, D = 256, order N = 3 (w = 93), tau = -0.2i (the headline workload).
+L = 100, D = 256, order N = 3 (w = 93), tau = -0.2i (the headline workload), by
+default with every contraction as exact Ozaki-scheme digit-slice GEMMs on the
+bf16 tensor cores (fp64-accurate) and fp64 QR and reductions.
 The state lives in HBM across steps; the
 environments (about 9.7 GB in fp64) are larger than L2, so no flush is needed.
 
 Usage:
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16x3|tf32x3|tf32|bf16x3+oz|...]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64+oz|fp64|bf16x3|bf16x3+oz|...]
   python bench.py --impl reference ...     # the fp64 oracle on the host cores
+  python bench.py --verify                 # every form to t = 5 against the oracle's stored values
+  python bench.py --c5                     # one step of each form on the full-size spin-1 chain
+  python bench.py --oracle-step            # one full oracle step on the host cores
+  python bench.py --probe <case>           # the fixed small workloads of the ncu captures
 Prints one JSON line (rank 0).
 """
 from __future__ import annotations
@@ -484,21 +490,99 @@ def verify(args):
 PROBES = ("kernels", "form", "fp64", "tc", "ozgemm", "qr")
 
 
+def oracle_step(args):
+    """One full oracle evolve_step of the headline chain on the host cores (the
+    thread count numpy's BLAS was started with: OPENBLAS_NUM_THREADS /
+    OMP_NUM_THREADS), from the product state (the oracle's tensors have the
+    workload's bond dimensions from the start, so every step costs the same).
+    With --oracle-updates U > 0 only the right-environment build and the first U
+    local updates of the first sweep are timed, and the step time is that
+    per-update time times the step's updates (stated as extrapolated)."""
+    from oracle import fit, mpo
+    cfg = wl.config(WORKLOAD)
+    L, D, sweeps = cfg["L"], cfg["D"], cfg["sweeps"]
+    W = mpo.build_mpo(*wl.model_blocks(cfg), cfg["N"], cfg["tau"])
+    psi = fit.product_mps(wl.initial_vectors(cfg), D)
+    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)))
+    line = {"impl": "oracle", "workload": WORKLOAD, "threads": threads, "host_cpus": os.cpu_count()}
+    if args.oracle_updates <= 0:
+        t0 = time.perf_counter()
+        fit.evolve_step(psi, W, sweeps, canonical=False)
+        dt = time.perf_counter() - t0
+        line.update({"s_per_step": dt, "sweeps_per_s": sweeps / dt, "measured": "one full evolve_step"})
+    else:
+        # interior local updates (full bond dimension on both sides) on seeded
+        # random operands of the step's shapes; the step is that time times its
+        # updates (the environment build counted as 3/4 of an update each)
+        rng = np.random.default_rng(7)
+        w = W[L // 2].shape[0]
+        cg = lambda *sh: (rng.standard_normal(sh) + 1j * rng.standard_normal(sh)) / math.sqrt(max(sh))
+        El, A, Er = cg(D, w, D), cg(D, cfg["d"], D), cg(D, w, D)
+        t1 = time.perf_counter()
+        for _ in range(args.oracle_updates):
+            fit._step_right(El, A, W[L // 2], Er)
+        t_up = (time.perf_counter() - t1) / args.oracle_updates
+        updates = sweeps * 2 * (L - 1) + 0.75 * (L - 1) + 1
+        dt = t_up * updates
+        line.update({"s_per_step": dt, "sweeps_per_s": sweeps / dt, "t_interior_update_s": t_up,
+                     "measured": f"{args.oracle_updates} interior local updates (T build, apply, Householder QR, "
+                                 f"environment); step = {updates:g} updates x that time (extrapolated)"})
+    print(json.dumps(line), flush=True)
+
+
+def c5_forms(args):
+    """The spin-1 workload at full size (L = 128, D = 512, N = 4, d = 3, w = 160,
+    tau = -0.25i, 2 sweeps): one time step in each form from the same state (the
+    state after --warmup steps of the form every contraction as Ozaki-scheme
+    GEMMs, so the bonds are populated), timed with CUDA events. The forms'
+    accuracy at this size comes from the reduced run of the same chain
+    (tests/test_gpu_c5.py)."""
+    import torch
+    import paper_2302_14181_gb300 as tv
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cfg = wl.config("spin1_L128_N4_D512")
+    tau, D = cfg["tau"], cfg["D"]
+    ctx = tv.Context()
+    W = tv.mpo_build(ctx, *wl.model_blocks(cfg), cfg["N"], tau)
+    psi = tv.mps_init(ctx, wl.initial_vectors(cfg), D)
+    for _ in range(args.warmup):
+        tv.evolve_step(psi, W, tau, D, cfg["sweeps"], PREC["fp64+oz"])
+    dims = psi.bond_dims()
+    wd = W.bond_dims()
+    flops = step_flops(dims, wd[:-1], wd[1:], cfg["d"], cfg["sweeps"])
+    stream = torch.cuda.current_stream()
+    out = {"workload": "spin1_L128_N4_D512", "L": cfg["L"], "D": D, "N": cfg["N"], "w": max(wd),
+           "warmup_steps": args.warmup, "useful_tflop_per_step": flops / 1e12, "forms": {}}
+    for name in args.c5_forms.split(","):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tv.evolve_step(psi, W, tau, D, cfg["sweeps"], PREC[name])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["forms"][name] = {"s_per_step": ms / 1e3, "sweeps_per_s": cfg["sweeps"] / (ms / 1e3),
+                              "useful_tflops": flops / (ms / 1e3) / 1e12}
+        print(json.dumps({"form": name, **out["forms"][name]}), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def probe(args):
     """One fixed workload per case, on the long-range Ising chain at length
     --probe-L (the per-site shapes of the L = 100 chain at its interior sites):
       kernels  every form of evolve_step once from the product state (fp64 with
                1 sweep; bf16x3, bf16x3 tensor-core only and bf16x3 + Ozaki with
                2), observables after each, then one overlap;
-      form     two steps of tf32x3 + Ozaki, 2 sweeps each;
+      form     two steps of the benchmark's form (every contraction as
+               Ozaki-scheme GEMMs), 2 sweeps each;
       fp64     one fp64 step, 1 sweep;
       tc       one bf16x3 and one tf32x3 tensor-core-only step, each from the
                product state, with --probe-sweeps sweeps;
       ozgemm   the Ozaki-scheme GEMM alone at the interior-site shapes, timed
                with the library's events (kernel and slicing per launch);
-      qr       two untimed steps of tf32x3 + Ozaki, then three steps with the
-               library's events on: QR factorisation and Q formation time per
-               step and per call."""
+      qr       two untimed steps of the benchmark's form, then three steps with
+               the library's events on: QR factorisation and Q formation time
+               per step and per call."""
     import torch
     import paper_2302_14181_gb300 as tv
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -519,7 +603,7 @@ def probe(args):
     elif case == "form":
         psi = tv.mps_init(ctx, v0, D)
         for _ in range(2):
-            tv.evolve_step(psi, W, tau, D, 2, tv.TF32X3 | tv.OZAKI)
+            tv.evolve_step(psi, W, tau, D, 2, PREC["fp64+oz"])
     elif case == "fp64":
         psi = tv.mps_init(ctx, v0, D)
         tv.evolve_step(psi, W, tau, D, 1, tv.FP64)
@@ -552,14 +636,14 @@ def probe(args):
     elif case == "qr":
         psi = tv.mps_init(ctx, v0, D)
         for _ in range(2):
-            tv.evolve_step(psi, W, tau, D, 2, tv.TF32X3 | tv.OZAKI)
+            tv.evolve_step(psi, W, tau, D, 2, PREC["fp64+oz"])
         torch.cuda.synchronize()
         ctx.prof_enable(True)
         for c in (tv._lib.PROF_QR, tv._lib.PROF_FORMQ):
             ctx.prof_read(c)
         t0 = time.perf_counter()
         for _ in range(3):
-            tv.evolve_step(psi, W, tau, D, 2, tv.TF32X3 | tv.OZAKI)
+            tv.evolve_step(psi, W, tau, D, 2, PREC["fp64+oz"])
         torch.cuda.synchronize()
         step_s = (time.perf_counter() - t0) / 3
         qms, qn, _, _ = ctx.prof_read(tv._lib.PROF_QR)
@@ -584,13 +668,23 @@ def main():
     ap.add_argument("--sweeps", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--verify", action="store_true", help="run the t = 5 evolution in each form against the oracle")
-    ap.add_argument("--verify-forms", default="bf16x3+oz,tf32x3+oz,fp64+oz,bf16x3,fp64")
+    ap.add_argument("--verify-forms", default="fp64+oz,bf16x3+oz,bf16x3,fp64")
     ap.add_argument("--probe", choices=PROBES, help="run one fixed small workload (for ncu captures) instead")
     ap.add_argument("--probe-L", type=int, default=20)
     ap.add_argument("--probe-sweeps", type=int, default=1)
+    ap.add_argument("--c5", action="store_true", help="time one step of each form on the full-size spin-1 chain")
+    ap.add_argument("--oracle-step", action="store_true", help="time one full oracle step on the host cores")
+    ap.add_argument("--oracle-updates", type=int, default=0)
+    ap.add_argument("--c5-forms", default="fp64+oz,bf16x3+oz,bf16x3,fp64")
     args = ap.parse_args()
     if args.probe:
         probe(args)
+        return
+    if args.c5:
+        c5_forms(args)
+        return
+    if args.oracle_step:
+        oracle_step(args)
         return
     if args.verify:
         verify(args)

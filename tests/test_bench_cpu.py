@@ -160,10 +160,10 @@ def test_probe_cases_issue_their_calls(monkeypatch, capsys):
         "kernels": [("init", 256), ("step", 1, 0), ("measure",), ("init", 256), ("step", 2, 3), ("measure",),
                     ("init", 256), ("step", 2, 0x103), ("measure",), ("init", 256), ("step", 2, 0x203),
                     ("measure",), ("init", 256)],
-        "form": [("init", 256), ("step", 2, 0x202), ("step", 2, 0x202)],
+        "form": [("init", 256), ("step", 2, 0x200), ("step", 2, 0x200)],
         "fp64": [("init", 256), ("step", 1, 0)],
         "tc": [("init", 256), ("step", 1, 0x103), ("init", 256), ("step", 1, 0x102)],
-        "qr": [("init", 256)] + [("step", 2, 0x202)] * 5,
+        "qr": [("init", 256)] + [("step", 2, 0x200)] * 5,
     }
     for case in bench.PROBES:
         calls.clear()
