@@ -360,17 +360,29 @@ def our_arm(args):
     h2d = sum(h.nbytes for h in host)
     d2h = h2d + 16 * len(ops) * cfg["L"]
     e2e_steps = max(1, args.steps)
+    parts = {"upload_s": 0.0, "evolve_s": 0.0, "measure_s": 0.0, "download_s": 0.0}
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
+        ta = time.perf_counter()
         for i in range(cfg["L"]):
             psi.set_site(i, host[i])
-        tv.evolve_step(psi, W, tau, D, sweeps, prec)
-        tv.measure_local(psi, ops)
+        torch.cuda.synchronize()
+        tb = time.perf_counter()
+        tv.evolve_step(psi, W, tau, D, sweeps, prec)      # synchronises (reads the step's device flags)
+        tc = time.perf_counter()
+        tv.measure_local(psi, ops)                        # synchronises
+        td = time.perf_counter()
         for i in range(cfg["L"]):
             host[i][...] = psi.site(i)
+        te = time.perf_counter()
+        parts["upload_s"] += tb - ta
+        parts["evolve_s"] += tc - tb
+        parts["measure_s"] += td - tc
+        parts["download_s"] += te - td
     barrier()
     t_e2e = time.perf_counter() - t0
+    parts = {k: v / e2e_steps for k, v in parts.items()}
     e2e_val, _ = replica_throughput(1e3 * t_e2e, e2e_steps * sweeps, "cuda")
 
     if rank == 0:
@@ -436,7 +448,8 @@ def our_arm(args):
                              "sample": f"{cpu['updates']} oracle local updates at the interior-site shape "
                                        f"(D=256, w=93, d=2; {cpu['t_update_s']:.2f} s each) scaled to one "
                                        f"evolve_step of the L=100 chain"},
-            "e2e": {"value": e2e_val, "unit": "sweeps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_val, "unit": "sweeps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "parts_per_step": parts},
             "gpu_launches": launches,
             "obs_error": obs_err,
             "fp64_form": fp64_form,

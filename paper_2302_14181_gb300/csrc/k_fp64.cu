@@ -761,15 +761,19 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
       s_tau[k & 1] = s_refl.tau;
       tau[k] = s_refl.tau;
       beta[k] = s_refl.beta;
+      // tau_k also rides in row k - 1 of V's column k (above the reflector, a
+      // row no reader of V uses otherwise), so a consumer fetches it together
+      // with the reflector's rows instead of in a dependent load of its own
+      if (k > 0) V[(long long)k * m + k - 1] = s_refl.tau;
     }
     // the block barrier orders every thread's stores of V before thread 0's
     // release store, which is cumulative over them (one release per block)
     __syncthreads();
     if (threadIdx.x == 0) st_release(flags + k, epoch);
-    // rows above k: zeros of V, and the R part of column k for qr64_extract_r
+    // rows above k - 1: zeros of V, and the R part of column k for qr64_extract_r
     const double2* col = cols + (size_t)(k / G) * m;
     for (int r = threadIdx.x; r < k; r += blockDim.x) {
-      V[(long long)k * m + r] = make_double2(0.0, 0.0);
+      if (r + 1 < k) V[(long long)k * m + r] = make_double2(0.0, 0.0);
       A[(long long)k * m + r] = col[r];
     }
   };
@@ -794,15 +798,17 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
             }
           }
         }
-        if (!s_abort) s_tau[k & 1] = __ldcg(tau + k);
       }
       __syncthreads();
       if (s_abort) return;
       // each thread loads the rows it reads first (its own rows of the dot
       // products below); other threads read them only after a reduction's
-      // barrier
+      // barrier. tau_k comes from row k - 1 of the column (tau[0] for k = 0),
+      // in the same round of loads.
       const double2* Vk = V + (long long)k * m;
       for (int r = k + threadIdx.x; r < m; r += blockDim.x) v[r] = __ldcg(Vk + r);  // L2, never a stale L1 line
+      if (threadIdx.x == blockDim.x - 1) s_tau[k & 1] = k > 0 ? __ldcg(Vk + k - 1) : __ldcg(tau);
+      __syncthreads();
     }
     const double2 t = s_tau[k & 1];
     // look-ahead: column k + 1 first, then publish reflector k + 1
