@@ -15,6 +15,8 @@ Usage:
   python bench.py --verify                 # every form to t = 5 against the oracle's stored values
   python bench.py --c5                     # one step of each form on the full-size spin-1 chain
   python bench.py --oracle-step            # one full oracle step on the host cores
+  python bench.py --splitting              # complex-step splitting vs the native order-2 MPO
+  python bench.py --cylinder               # fidelity density vs time step, 2-D TFI cylinder
   python bench.py --probe <case>           # the fixed small workloads of the ncu captures
 Prints one JSON line (rank 0).
 """
@@ -350,6 +352,44 @@ def our_arm(args):
                                  "speedup_of_measured_form": (fms / (ms_max / args.steps))}
         fp64_form = other_forms.get("fp64")
 
+    # the batched form (64 independent TFI/XXZ chains of uneven size, complex
+    # fp32-class contractions with fp64 QR, one graph replay per step) against
+    # looping the single-chain call over the same chains
+    batched = None
+    if not args.no_fp64_compare:
+        chains = wl.batched_chains()
+        bW = [tv.mpo_build(ctx, *wl.model_blocks(c), c["N"], c["tau"]) for c in chains]
+        bprec = PREC["tc-tf32x3"]
+        bsw = chains[0]["sweeps"]
+        bps = [tv.mps_init(ctx, wl.initial_vectors(c), c["D"]) for c in chains]
+        for _ in range(8):        # schedule timing, two graph captures, replays
+            tv.evolve_step_batched(bps, bW, bsw, bprec)
+        barrier()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(3):
+            tv.evolve_step_batched(bps, bW, bsw, bprec)
+        b1.record(stream)
+        barrier()
+        bms = b0.elapsed_time(b1) / 3
+        lps = [tv.mps_init(ctx, wl.initial_vectors(c), c["D"]) for c in chains]
+        for c, p_, w_ in zip(chains, lps, bW):
+            tv.evolve_step(p_, w_, c["tau"], c["D"], bsw, bprec)
+        barrier()
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        for c, p_, w_ in zip(chains, lps, bW):
+            tv.evolve_step(p_, w_, c["tau"], c["D"], bsw, bprec)
+        l1.record(stream)
+        barrier()
+        lms = l0.elapsed_time(l1)
+        batched = {"workload": "64 chains: TFI/XXZ, J per bond U[0.5,1.5], L in [16,80], D in {32,64,128}, "
+                               "N in {2,3}, tau=-0.1i",
+                   "precision": "tc-tf32x3 (tf32x3 contractions, fp64 QR)", "sweeps": bsw,
+                   "ms_per_step": bms, "chain_sweeps_per_s": len(chains) * bsw / (bms / 1e3),
+                   "looped_ms_per_step": lms, "looped_chain_sweeps_per_s": len(chains) * bsw / (lms / 1e3)}
+        del bps, lps, bW
+
     # end to end through the public API with host buffers (pinned), every step:
     # upload the state, evolve, read observables and the state back
     ops = [wl.pauli()[0], wl.pauli()[2]]
@@ -454,6 +494,7 @@ def our_arm(args):
             "obs_error": obs_err,
             "fp64_form": fp64_form,
             "other_forms": other_forms,
+            "batched": batched,
             "clocks": clocks.summary(),
             "kernel_ms": {name: prof[c][0] for c, name in enumerate(PROF_NAMES)},
         }
@@ -500,7 +541,7 @@ def verify(args):
 # small, fixed invocations for ncu captures (the commands in profiles/)
 # ----------------------------------------------------------------------------
 
-PROBES = ("kernels", "form", "fp64", "tc", "ozgemm", "qr")
+PROBES = ("kernels", "form", "fp64", "tc", "ozgemm", "qr", "batched", "twosite")
 
 
 def oracle_step(args):
@@ -541,6 +582,110 @@ def oracle_step(args):
                      "measured": f"{args.oracle_updates} interior local updates (T build, apply, Householder QR, "
                                  f"environment); step = {updates:g} updates x that time (extrapolated)"})
     print(json.dumps(line), flush=True)
+
+
+def splitting_study(args):
+    """Sec. 8.3's comparison at scale: the XXZ chain (Neel start, D = 64) at
+    L in {16, 64} and dt in {0.1, 0.2, 0.4}: 10 steps of the native order-2 MPO
+    (bond 1 + chi + chi^2 = 13) against 10 pairs of order-1 MPOs at the complex
+    steps dt (1 +- i)/2 (bond 1 + chi = 4 each), fp64 form, 2 sweeps per step.
+    Reported per case: seconds per time step of each scheme (CUDA events), the
+    log-norm change per step of each, and the largest log-norm of the first
+    (amplifying, Re tau > 0) factor: the growth that truncation errors in
+    high-energy components see between the two factors."""
+    import torch
+    import paper_2302_14181_gb300 as tv
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ctx = tv.Context()
+    stream = torch.cuda.current_stream()
+    D, nsteps = 64, 10
+    for L in (16, 64):
+        blocks = wl.xxz_blocks(L, 0.5)
+        v0 = wl.product_state("neel", L)
+        for dt in (0.1, 0.2, 0.4):
+            tau = -1j * dt
+            taus = (tau * (1 + 1j) / 2, tau * (1 - 1j) / 2)
+            W2 = tv.mpo_build(ctx, *blocks, 2, tau)
+            W1 = [tv.mpo_build(ctx, *blocks, 1, x) for x in taus]
+            out = {"L": L, "dt": dt, "D": D, "steps": nsteps, "w_native": W2.bond_dims()[L // 2],
+                   "w_split": W1[0].bond_dims()[L // 2]}
+            for name in ("native", "split"):
+                psi = tv.mps_init(ctx, v0, D)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                first = []
+                ln0 = psi.log_norm()
+                for _ in range(nsteps):
+                    if name == "native":
+                        tv.evolve_step(psi, W2, tau, D, 2, tv.FP64)
+                    else:
+                        l0 = psi.log_norm()
+                        tv.evolve_step(psi, W1[0], taus[0], D, 2, tv.FP64)
+                        first.append(psi.log_norm() - l0)
+                        tv.evolve_step(psi, W1[1], taus[1], D, 2, tv.FP64)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                out[name] = {"s_per_step": e0.elapsed_time(e1) / 1e3 / nsteps,
+                             "log_norm_per_step": (psi.log_norm() - ln0) / nsteps}
+                if first:
+                    out[name]["first_factor_log_norm_max"] = max(first)
+            print(json.dumps(out), flush=True)
+
+
+def cylinder_study(args):
+    """The paper's efficiency workload (Sec. 8.2) on a finite cylinder: the 2-D
+    transverse-field Ising model, circumference 4 with spiral boundary
+    conditions (chi = 4), length --cyl-Lx, g = 3.5 (paramagnetic side), bond
+    dimension D. A ground state by imaginary time (60 steps of tau = -0.1, order
+    3, from a seeded random state), the middle spin flipped, then evolution to
+    T = 1 with step dt and MPO order N, against a reference with dt = 0.01 at
+    order 3: the fidelity density f = log|<ref|psi>| / L and the wall time of
+    each run (fp64 form, 2 sweeps per step)."""
+    import torch
+    import paper_2302_14181_gb300 as tv
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ctx = tv.Context()
+    Wc, Lx, g, D = 4, args.cyl_Lx, 3.5, args.cyl_D
+    L = Wc * Lx
+    blocks = wl.tfi_cylinder_blocks(Lx, Wc, g)
+    X = wl.pauli()[0]
+    plus = np.tile(np.array([1.0, 1.0], np.complex128) / math.sqrt(2), (L, 1))
+    gs = tv.mps_init(ctx, plus, D)
+    for i, a in enumerate(wl.random_mps(L, 2, D, seed=9)):
+        gs.set_site(i, a)
+    Wg = tv.mpo_build(ctx, *blocks, 3, -0.1)
+    for _ in range(60):
+        tv.evolve_step(gs, Wg, -0.1, D, 2, tv.FP64)
+    sites = [gs.site(i) for i in range(L)]
+    sites[L // 2] = np.einsum("st,atb->asb", X, sites[L // 2])
+
+    def start():
+        psi = tv.mps_init(ctx, plus, D)
+        for i in range(L):
+            psi.set_site(i, sites[i])
+        return psi
+
+    def run(N, dt):
+        W = tv.mpo_build(ctx, *blocks, N, -1j * dt)
+        psi = start()
+        n = int(round(1.0 / dt))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            tv.evolve_step(psi, W, -1j * dt, D, 2, tv.FP64)
+        torch.cuda.synchronize()
+        return psi, time.perf_counter() - t0, W.bond_dims()[L // 2]
+
+    ref, t_ref, _ = run(3, 0.01)
+    print(json.dumps({"cylinder": f"W=4 x Lx={Lx}", "L": L, "D": D, "g": g, "reference": "N=3, dt=0.01",
+                      "reference_s": t_ref}), flush=True)
+    for N in (1, 2, 3):
+        for dt in (0.25, 0.2, 0.1, 0.05):
+            psi, secs, w = run(N, dt)
+            la, _ = tv.mps_overlap(ref, psi)
+            print(json.dumps({"N": N, "w": w, "dt": dt, "steps": int(round(1.0 / dt)), "seconds": secs,
+                              "fidelity_density": la / L}), flush=True)
 
 
 def c5_forms(args):
@@ -595,7 +740,11 @@ def probe(args):
                with the library's events (kernel and slicing per launch);
       qr       two untimed steps of the benchmark's form, then three steps with
                the library's events on: QR factorisation and Q formation time
-               per step and per call."""
+               per step and per call;
+      batched  the first 8 chains of the batched workload, three batched steps
+               (tensor-core tf32x3 contractions, fp64 QR one launch per column);
+      twosite  one step of the two-site fit (fp64) on the XXZ chain L = 16,
+               D = 64, order 3, from the Neel state."""
     import torch
     import paper_2302_14181_gb300 as tv
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -665,6 +814,17 @@ def probe(args):
         print(json.dumps({"step_s": step_s, "qr_ms_per_step": qms / 3, "qr_calls_per_step": qn / 3,
                           "qr_ms_per_call": qms / max(1, qn), "form_q_ms_per_step": fms / 3,
                           "form_q_ms_per_call": fms / max(1, fn)}), flush=True)
+    elif case == "batched":
+        chains = wl.batched_chains()[:8]
+        bW = [tv.mpo_build(ctx, *wl.model_blocks(c), c["N"], c["tau"]) for c in chains]
+        bps = [tv.mps_init(ctx, wl.initial_vectors(c), c["D"]) for c in chains]
+        for _ in range(3):
+            tv.evolve_step_batched(bps, bW, 1, PREC["tc-tf32x3"])
+    elif case == "twosite":
+        xc = wl.config("xxz_L64_N3", L=16, D=64)
+        xW = tv.mpo_build(ctx, *wl.model_blocks(xc), xc["N"], xc["tau"])
+        xp = tv.mps_init(ctx, wl.initial_vectors(xc), xc["D"])
+        tv.evolve_step(xp, xW, xc["tau"], xc["D"], 1, tv.FP64 | tv.TWO_SITE)
     torch.cuda.synchronize()
     print(json.dumps({"probe": case, "L": cfg["L"], "launches": ctx.launch_count()}), flush=True)
 
@@ -687,6 +847,10 @@ def main():
     ap.add_argument("--probe-sweeps", type=int, default=1)
     ap.add_argument("--c5", action="store_true", help="time one step of each form on the full-size spin-1 chain")
     ap.add_argument("--oracle-step", action="store_true", help="time one full oracle step on the host cores")
+    ap.add_argument("--splitting", action="store_true", help="complex-step splitting against the native order-2 MPO")
+    ap.add_argument("--cylinder", action="store_true", help="fidelity density vs time step on the 2-D TFI cylinder")
+    ap.add_argument("--cyl-Lx", type=int, default=8)
+    ap.add_argument("--cyl-D", type=int, default=64)
     ap.add_argument("--oracle-updates", type=int, default=0)
     ap.add_argument("--c5-forms", default="fp64+oz,bf16x3+oz,bf16x3,fp64")
     args = ap.parse_args()
@@ -698,6 +862,12 @@ def main():
         return
     if args.oracle_step:
         oracle_step(args)
+        return
+    if args.splitting:
+        splitting_study(args)
+        return
+    if args.cylinder:
+        cylinder_study(args)
         return
     if args.verify:
         verify(args)

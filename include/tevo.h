@@ -69,6 +69,19 @@ extern "C" {
  * pipe is about 1/1600 of its bf16 tensor rate. */
 #define TEVO_OZAKI 0x200
 #define TEVO_OZAKI_SLICES(g) (TEVO_OZAKI | ((g) << 12))
+/* OR-ed into TEVO_FP64 (with or without TEVO_OZAKI): the two-site form of the
+ * variational fit (Sec. 2.2, the (i)DMRG row of Table 1 in its two-site form).
+ * Each update contracts the target W|psi> on the environments of two
+ * neighbouring sites into Theta ((D_l d) x (d D_r)), orthogonalises the columns
+ * of Theta by one-sided Jacobi rotations in fp64 (its left singular vectors
+ * times the singular values), keeps the D_i of largest norm and re-gauges them
+ * with the fp64 Householder QR; the site keeps Q, the environment grows through
+ * conj(Q). The bond basis is thus chosen from the target's singular vectors on
+ * the pair, so a rank-deficient start needs no completion rule. Costs about
+ * twice the single-site update plus the Jacobi rotations. Other forms with
+ * this flag, and the batched form, are refused (TEVO_EINVAL /
+ * TEVO_EUNSUPPORTED). */
+#define TEVO_TWO_SITE 0x400
 
 /* variants of the MPO construction (Secs. 3-6 of the paper) */
 #define TEVO_MPO_PLAIN 0     /* Algorithm 1 only (Eq. W1 at N = 1, Eq. W2 at N = 2) */

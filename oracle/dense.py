@@ -7,9 +7,14 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   * ``mpo_to_dense`` contracts per-site W_i[w_l, s, s', w_r] into a d^L x d^L
     matrix with the boundary vectors of Eq. boundary already sliced in.
   * ``expm_tau_h`` is exp(tau H) from numpy.linalg.eigh of the Hermitian H.
+  * ``thermal_expect`` is the Gibbs average Tr(O_i e^{-beta H}) / Tr(e^{-beta H})
+    of single-site operators, also from eigh (the finite-temperature states of
+    Sec. 8.4, here on a finite chain).
 
 Pins: tests/test_oracle_fit.py checks the expansion against Kronecker-sum
 Hamiltonians written directly from the model definitions, and eigh against
+scipy.linalg.expm; tests/test_oracle_thermal.py checks the Gibbs averages at
+beta = 0 (Tr O / d), at large beta (the ground state's values) and against
 scipy.linalg.expm.
 """
 from __future__ import annotations
@@ -91,4 +96,19 @@ def expect_dense(v, ops, L):
     for k, O in enumerate(ops):
         for i in range(L):
             out[k, i] = np.vdot(v, local_op(O, i, L) @ v) / n
+    return out
+
+
+def thermal_expect(H, beta, ops, L):
+    """Tr(O_i e^{-beta H}) / Tr(e^{-beta H}) for every operator and site;
+    [len(ops), L]. Eigenvalues are shifted by the smallest one before the
+    exponential (the shift cancels in the ratio)."""
+    e, U = np.linalg.eigh(H)
+    w = np.exp(-beta * (e - e.min()))
+    rho = (U * w) @ U.conj().T
+    Z = np.trace(rho)
+    out = np.zeros((len(ops), L), np.complex128)
+    for k, O in enumerate(ops):
+        for i in range(L):
+            out[k, i] = np.trace(local_op(O, i, L) @ rho) / Z
     return out

@@ -209,6 +209,66 @@ def evolve_step(psi, W, sweeps=1, canonical=False):
     return phi, float(np.log(nrm))
 
 
+def two_site_theta(Lenv, A1, A2, W1, W2, Renv):
+    """Theta[(p s), (q s')] = sum L[p,w,a] A1[a,t,b] A2[b,t',c] W1[w,s,t,v]
+    W2[v,s',t',u] R[q,u,c]: the target W|psi> projected on the environments of
+    two neighbouring sites. Returns (Theta as a (Dp d) x (Dq d) matrix, the
+    left site's T of make_T, for the environment update)."""
+    T = make_T(Lenv, A1, W1)                                     # [p, s, v, b]
+    TR = make_T(Renv, mirror_site(A2), mirror_mpo(W2))           # [q, s', v, b]
+    p, d, v, b = T.shape
+    q = TR.shape[0]
+    return T.reshape(p * d, v * b) @ TR.reshape(q * d, v * b).T, T
+
+
+def _two_site_right(Lenv, A1, A2, W1, W2, Renv, k):
+    """One rightward two-site update: the k leading left singular vectors of
+    Theta become the left site (Q = U[:, :k], left-canonical) and the left
+    environment grows through conj(Q)."""
+    theta, T = two_site_theta(Lenv, A1, A2, W1, W2, Renv)
+    U, _, _ = np.linalg.svd(theta, full_matrices=False)
+    Q = U[:, :k].reshape(Lenv.shape[0], A1.shape[1], k)
+    return Q, env_next(Q, T)
+
+
+def evolve_step_two_site(psi, W, sweeps=1, canonical=False):
+    """One time step |psi> -> W|psi> fitted by two-site updates at the bond
+    dimensions of psi (the (i)DMRG row of Table 1 in its two-site form, Sec. 2.2).
+
+    As evolve_step, but each update treats a pair of neighbouring sites: the
+    target projected on their environments, Theta, is cut by its singular value
+    decomposition (numpy.linalg.svd) and the leading D_i singular vectors become
+    the site moving away from the pair's far side. The basis of every bond is
+    chosen from the target's Schmidt decomposition on the pair, so a bond can
+    take directions that the guess phi = psi does not contain (a rank-deficient
+    start needs no completion rule). One sweep = pairs (1,2)..(L-1,L) moving
+    right, then (L,L-1)..(2,1) moving left; the centre is then recomputed at
+    site 1 and normalised as in evolve_step. Returns (phi, log_norm)."""
+    L = len(psi)
+    phi = [x.copy() for x in psi] if canonical else right_canonicalize(psi)
+    one = np.ones((1, 1, 1), np.complex128)
+    Renv = [None] * (L + 1)
+    Renv[L] = one
+    for i in range(L - 1, 0, -1):
+        Renv[i] = env_from_site(Renv[i + 1], mirror_site(phi[i]), mirror_site(psi[i]), mirror_mpo(W[i]))
+    Lenv = [None] * (L + 1)
+    Lenv[0] = one
+    for _ in range(sweeps):
+        for i in range(0, L - 1):
+            k = psi[i].shape[2]
+            phi[i], Lenv[i + 1] = _two_site_right(Lenv[i], psi[i], psi[i + 1], W[i], W[i + 1], Renv[i + 2], k)
+        for i in range(L - 1, 0, -1):
+            k = psi[i].shape[0]
+            Qm, Renv[i] = _two_site_right(Renv[i + 1], mirror_site(psi[i]), mirror_site(psi[i - 1]),
+                                          mirror_mpo(W[i]), mirror_mpo(W[i - 1]), Lenv[i - 1], k)
+            phi[i] = mirror_site(Qm)
+    Tm = make_T(Renv[1], mirror_site(psi[0]), mirror_mpo(W[0]))
+    centre = mirror_site(apply_T(Tm, Lenv[0]))
+    nrm = np.sqrt(np.sum(np.abs(centre) ** 2))
+    phi[0] = centre / nrm
+    return phi, float(np.log(nrm))
+
+
 def evolve(psi, W, steps, sweeps=1, canonical=False, observe=None):
     """Repeated time steps; returns (psi, total log norm, [observe(psi) per step])."""
     logn = 0.0

@@ -20,13 +20,13 @@ import os
 import numpy as np
 
 from . import _lib
-from ._lib import (FP64, TF32, TF32X3, BF16X3, TC_ONLY, OZAKI, OZAKI_SLICES, MPO_PLAIN, MPO_EXACT,  # noqa: F401
+from ._lib import (FP64, TF32, TF32X3, BF16X3, TC_ONLY, OZAKI, OZAKI_SLICES, TWO_SITE, MPO_PLAIN, MPO_EXACT,  # noqa: F401
                    MPO_EXTENDED, MPO_FULL, TevoError)
 
 __all__ = [
     "Context", "MPO", "MPS", "mpo_build", "mpo_build_host", "mps_init", "evolve_step", "evolve_step_batched", "measure_local", "mps_overlap",
     "tevo_gemm", "tevo_gemm_noalloc", "tevo_wait_selftest", "tevo_strerror",
-    "FP64", "TF32", "TF32X3", "BF16X3", "TC_ONLY", "OZAKI", "OZAKI_SLICES", "MPO_PLAIN", "MPO_EXACT", "MPO_EXTENDED", "MPO_FULL",
+    "FP64", "TF32", "TF32X3", "BF16X3", "TC_ONLY", "OZAKI", "OZAKI_SLICES", "TWO_SITE", "MPO_PLAIN", "MPO_EXACT", "MPO_EXTENDED", "MPO_FULL",
     "TevoError", "library_path",
 ]
 

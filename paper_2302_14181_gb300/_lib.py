@@ -18,6 +18,7 @@ lib = ctypes.CDLL(LIB_PATH)
 FP64, TF32, TF32X3, BF16X3 = 0, 1, 2, 3
 TC_ONLY = 0x100
 OZAKI = 0x200
+TWO_SITE = 0x400
 
 
 def OZAKI_SLICES(g):

@@ -124,9 +124,11 @@ struct tevo_mps_s {
   Buf env, X, T, Bq, V, tau, beta, Atmp, Rm, gemm_ws, red;
   Buf qrflags;        // [0] error flag of the cooperative QR, [1..] reflector flags
   Buf qrwy;           // Gram matrices and triangular factors of the WY blocks (Q formation)
+  Buf T2, Th, jac;    // two-site form: the partner site's T, the two-site matrix, Jacobi workspace
   int qr_epoch = 0;
   bool coop_qr = true;  // off while a batched step issues (concurrent streams, graph capture)
   int oz_slices = 0;    // > 0 while a step runs its fp64 contractions as Ozaki-scheme GEMMs
+  bool two_site = false;  // the step in progress fits pairs of sites (TEVO_TWO_SITE)
   Buf oz_ws;            // digit slices, row exponents and split partials of those GEMMs
   int wmax = 0;
   MixedState* mixed = nullptr;
@@ -192,7 +194,8 @@ struct StepDims {
 // G1 + G2: T from (El, A, Wg) in fp64; G2 skips the MPO's zero entries when
 // its CSR form (sidx = row_ptr then col_idx, sval) is given
 int make_T64(tevo_mps s, const StepDims& k, const z64* El, const z64* A, const z64* Wg, const Buf* sidx = nullptr,
-             const Buf* sval = nullptr) {
+             const Buf* sval = nullptr, void* Tout = nullptr) {
+  void* T = Tout ? Tout : s->T.p;
   // G1: X[(p w), (s' b)] = El[(p w), a] A[a, (s' b)]
   TRY(gemm(s, gd(El, 0, k.Da, 1, A, 0, (long long)k.d * k.Db, 1, s->X.p, 0, (long long)k.d * k.Db, 1,
                  k.Dp * k.wl, k.d * k.Db, k.Da, 1)));
@@ -201,12 +204,12 @@ int make_T64(tevo_mps s, const StepDims& k, const z64* El, const z64* A, const z
   if (sidx && sidx->p && s->oz_slices == 0) {
     const int R = k.d * k.wr;
     const int* rp = static_cast<const int*>(sidx->p);
-    int e = zsparse_g2(launch_of(s->ctx), zp(s->X), zp(s->T), rp, rp + R + 1, static_cast<const z64*>(sval->p), R,
-                       k.wl * k.d, k.Db, k.Dp);
+    int e = zsparse_g2(launch_of(s->ctx), zp(s->X), static_cast<z64*>(T), rp, rp + R + 1,
+                       static_cast<const z64*>(sval->p), R, k.wl * k.d, k.Db, k.Dp);
     if (e != TEVO_EUNSUPPORTED) return e;
   }
   // G2: T_p[(s v), b] = Wg[(s v), (w s')] X_p[(w s'), b]
-  TRY(gemm(s, gd(Wg, 0, (long long)k.wl * k.d, 1, s->X.p, (long long)k.wl * k.d * k.Db, k.Db, 1, s->T.p,
+  TRY(gemm(s, gd(Wg, 0, (long long)k.wl * k.d, 1, s->X.p, (long long)k.wl * k.d * k.Db, k.Db, 1, T,
                  (long long)k.d * k.wr * k.Db, k.Db, 1, k.d * k.wr, k.Db, k.wl * k.d, k.Dp)));
   return 0;
 }
@@ -347,6 +350,77 @@ int sweep64(tevo_mps s, tevo_mpo W) {
     TRY(store_left(s, zp(s->Bq), zp(s->Anew[i]), k.Dq, d, k.Dp));
     TRY(env64(s, k, zp(s->Bq), env_slot(s, i)));
   }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// two-site fit: the pair (i, i+1) in the rightward layout (rightward = true:
+// site i keeps the leading left singular vectors of Theta) or the pair
+// (i-1, i) on the mirrored chain (rightward = false: site i keeps them)
+// ---------------------------------------------------------------------------
+int two_site_workspace(tevo_mps s, tevo_mpo W) {
+  tevo_ctx c = s->ctx;
+  const int d = s->d;
+  size_t xt = 0, md = 0;
+  for (int i = 0; i < s->L; ++i) {
+    xt = std::max({xt, (size_t)s->dims[i] * W->wl[i] * d * s->dims[i + 1],
+                   (size_t)s->dims[i + 1] * W->wr[i] * d * s->dims[i]});
+    md = std::max(md, (size_t)s->dims[i] * d);
+  }
+  md = std::max(md, (size_t)s->dims[s->L] * d);
+  TRY(ensure(c, s->T2, sizeof(z64) * xt));
+  TRY(ensure(c, s->Th, sizeof(z64) * md * (md + 1)));
+  TRY(ensure(c, s->jac, jacobi_ws_bytes((int)md + 1)));
+  return 0;
+}
+
+int two_site_update(tevo_mps s, tevo_mpo W, int i, bool rightward) {
+  Launch L = launch_of(s->ctx);
+  const int d = s->d;
+  // kA: the site that keeps the singular vectors; kB: its partner (mirrored layout)
+  StepDims kA, kB;
+  const z64 *envA, *envB;
+  if (rightward) {
+    kA = right_dims(s, W, i);
+    kB = left_dims(s, W, i + 1);
+    TRY(make_T64(s, kA, env_slot(s, i), zp(s->A[i]), zp(W->Wr[i]), &W->Sr_idx[i], &W->Sr_val[i]));
+    TRY(mirror_site64(L, zp(s->A[i + 1]), zp(s->Atmp), s->dims[i + 1], d, s->dims[i + 2]));
+    TRY(make_T64(s, kB, env_slot(s, i + 2), zp(s->Atmp), zp(W->Wl[i + 1]), &W->Sl_idx[i + 1], &W->Sl_val[i + 1],
+                 s->T2.p));
+    envA = env_slot(s, i + 1);
+    envB = nullptr;
+  } else {
+    kA = left_dims(s, W, i);
+    kB = right_dims(s, W, i - 1);
+    TRY(mirror_site64(L, zp(s->A[i]), zp(s->Atmp), s->dims[i], d, s->dims[i + 1]));
+    TRY(make_T64(s, kA, env_slot(s, i + 1), zp(s->Atmp), zp(W->Wl[i]), &W->Sl_idx[i], &W->Sl_val[i]));
+    TRY(make_T64(s, kB, env_slot(s, i - 1), zp(s->A[i - 1]), zp(W->Wr[i - 1]), &W->Sr_idx[i - 1],
+                 &W->Sr_val[i - 1], s->T2.p));
+    envA = env_slot(s, i);
+    envB = nullptr;
+  }
+  (void)envB;
+  // Theta[(p s), (q s')] = sum_(v b) T[(p s), (v b)] T2[(q s'), (v b)], column-major (ld = M)
+  const int M = kA.Dp * d, N = kB.Dp * d, K = kA.wr * kA.Db;
+  if (kB.wr * kB.Db != K) return TEVO_ESHAPE;
+  const int Np = N + (N & 1);  // the Jacobi pairs columns: an odd count gets a zero column
+  if (Np > N) TRY(fill64(L, zp(s->Th) + (size_t)N * M, (size_t)M, 0.0, 0.0));
+  TRY(gemm(s, gd(s->T.p, 0, K, 1, s->T2.p, 0, 1, K, s->Th.p, 0, 1, M, M, N, K, 1)));
+  const int k = kA.Dq;
+  int* jerr = reinterpret_cast<int*>(scal(s, 6));
+  TRY(jacobi_top_columns(L, zp(s->Th), M, Np, k, zp(s->Bq), s->jac.p, jerr));
+  TRY(qr_q(s, M, k, false));
+  if (rightward) {
+    TRY(store_right(s, zp(s->Bq), zp(s->Anew[i]), kA.Dp, d, k));
+  } else {
+    TRY(store_left(s, zp(s->Bq), zp(s->Anew[i]), k, d, kA.Dp));
+  }
+  return env64(s, kA, zp(s->Bq), const_cast<z64*>(envA));
+}
+
+int sweep_two_site(tevo_mps s, tevo_mpo W) {
+  for (int i = 0; i + 1 < s->L; ++i) TRY(two_site_update(s, W, i, true));
+  for (int i = s->L - 1; i >= 1; --i) TRY(two_site_update(s, W, i, false));
   return 0;
 }
 
@@ -752,7 +826,7 @@ extern "C" int mps_destroy(tevo_mps s) {
   for (auto& b : s->A) dfree(c, b);
   for (auto& b : s->Anew) dfree(c, b);
   for (Buf* b : {&s->scalars, &s->env, &s->X, &s->T, &s->Bq, &s->V, &s->tau, &s->beta, &s->Atmp, &s->Rm,
-                 &s->gemm_ws, &s->red, &s->qrflags, &s->qrwy, &s->oz_ws})
+                 &s->gemm_ws, &s->red, &s->qrflags, &s->qrwy, &s->T2, &s->Th, &s->jac, &s->oz_ws})
     dfree(c, *b);
   mixed_state_destroy(c, s->mixed);
   delete s;
@@ -777,6 +851,11 @@ int strip_oz(int precision) { return precision & ~(TEVO_OZAKI | (0xF << 12)); }
 
 int check_step_args(tevo_mps s, tevo_mpo W, int sweeps, int precision) {
   if (!s || !W || sweeps < 1) return TEVO_EINVAL;
+  // the two-site fit: the fp64 form only (its contractions may be Ozaki GEMMs)
+  if (precision & TEVO_TWO_SITE) {
+    if ((strip_oz(precision) & ~TEVO_TWO_SITE) != TEVO_FP64) return TEVO_EINVAL;
+    precision &= ~TEVO_TWO_SITE;
+  }
   const int oz = oz_slices_of(precision);
   if (oz < 0) return TEVO_EINVAL;
   precision = strip_oz(precision);
@@ -794,6 +873,8 @@ int check_step_args(tevo_mps s, tevo_mpo W, int sweeps, int precision) {
 int evolve_issue_body(tevo_mps s, tevo_mpo W, int sweeps, int precision, bool* mixed_out);
 
 int evolve_issue(tevo_mps s, tevo_mpo W, int sweeps, int precision, bool* mixed_out) {
+  s->two_site = (precision & TEVO_TWO_SITE) != 0;
+  precision &= ~TEVO_TWO_SITE;
   const int oz = oz_slices_of(precision);
   if (oz < 0) return TEVO_EINVAL;
   if (oz && cudaMemsetAsync(scal(s, OZ_FLAG_SLOT), 0, sizeof(double), s->ctx->stream) != cudaSuccess)
@@ -841,7 +922,13 @@ int evolve_issue_body(tevo_mps s, tevo_mpo W, int sweeps, int precision, bool* m
     TRY(mixed_centre(c, W, s, precision));
   } else {
     const int n64 = mixed ? 1 : sweeps;
-    for (int k = 0; k < n64; ++k) TRY(sweep64(s, W));
+    if (s->two_site) {
+      TRY(two_site_workspace(s, W));
+      TRYCUDA(cudaMemsetAsync(scal(s, 6), 0, sizeof(double), c->stream));
+      for (int k = 0; k < n64; ++k) TRY(sweep_two_site(s, W));
+    } else {
+      for (int k = 0; k < n64; ++k) TRY(sweep64(s, W));
+    }
     TRY(centre64(s, W));
   }
   TRY(finish_step(s));
@@ -852,14 +939,15 @@ int evolve_issue_body(tevo_mps s, tevo_mpo W, int sweeps, int precision, bool* m
 // device flags of the step just issued (synchronises the context stream)
 int evolve_check(tevo_mps s, bool mixed) {
   tevo_ctx c = s->ctx;
-  int flag = 0, tflag = 0, qflag = 0, oflag = 0;
+  int flag = 0, tflag = 0, qflag = 0, oflag = 0, jflag = 0;
   TRYCUDA(cudaMemcpyAsync(&flag, scal(s, 4), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  if (s->two_site) TRYCUDA(cudaMemcpyAsync(&jflag, scal(s, 6), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   TRYCUDA(cudaMemcpyAsync(&oflag, scal(s, OZ_FLAG_SLOT), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   if (s->qrflags.p)
     TRYCUDA(cudaMemcpyAsync(&qflag, s->qrflags.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   if (mixed) TRY(mixed_error_flag(c, s, &tflag));
   TRYCUDA(cudaStreamSynchronize(c->stream));
-  if (tflag || qflag || oflag) return TEVO_ETIMEOUT;
+  if (tflag || qflag || oflag || jflag) return TEVO_ETIMEOUT;
   if (flag) return TEVO_ENONFINITE;
   return 0;
 }
@@ -977,6 +1065,7 @@ extern "C" int evolve_step_batched(tevo_mps* psis, const tevo_mpo* Ws, int n, in
   if (!psis || !Ws || n < 1) return TEVO_EINVAL;
   for (int c = 0; c < n; ++c) TRY(check_step_args(psis[c], Ws[c], sweeps, precision));
   if (oz_slices_of(precision) != 0) return TEVO_EUNSUPPORTED;  // the Ozaki form is single-chain only
+  if (precision & TEVO_TWO_SITE) return TEVO_EUNSUPPORTED;     // so is the two-site fit
   for (int c = 0; c < n; ++c)
     for (int k = c + 1; k < n; ++k)
       if (psis[c] == psis[k]) return TEVO_EINVAL;
@@ -1168,7 +1257,13 @@ extern "C" int measure_local(tevo_mps s, int nops, const double* ops, double* ou
                      d * Dr, Dl, 1)));
       TRY(gemm(s, gd(s->A[i].p, 0, 1, Dr, Y.p, 0, Dr, 1, el + off[i + 1], 0, Dr, 1, Dr, Dr, Dl * d, 1, 1)));
     }
-    for (int i = L - 1; i >= 0; --i) {
+    // a state left by evolve_step is right-canonical from site 1 on (its sites
+    // are the isometries of the last leftward sweep): its right transfer
+    // matrices are identities
+    if (s->canonical) {
+      for (int i = 1; i < L; ++i) TRY(eye64(Lc, er + off[i], s->dims[i]));
+    }
+    for (int i = L - 1; i >= 0 && !s->canonical; --i) {
       const int Dl = s->dims[i], Dr = s->dims[i + 1];
       TRY(mirror_site64(Lc, zp(s->A[i]), zp(s->Atmp), Dl, d, Dr));
       TRY(gemm(s, gd(er + off[i + 1], 0, Dr, 1, s->Atmp.p, 0, (long long)d * Dl, 1, Y.p, 0, (long long)d * Dl, 1,

@@ -294,6 +294,8 @@ constexpr int QR_THREADS = 128;
 #define QR_COOP_MAX_CTAS 1024
 #endif
 constexpr double DEFLATE = 2.2737367544323206e-13;  // 2^-42
+constexpr int JAC_MAX_SWEEPS = 40;
+constexpr double JAC_TOL = 1e-15;
 
 // Block reductions. Lane 0 of each warp ends with the warp's sum; at offset o
 // only lanes below o feed a lane that a later offset reads, so the others skip
@@ -508,19 +510,28 @@ __global__ void qr_wy_gram_kernel(const double2* V, int m, int n, double2* G) {
   }
 }
 
-// T_b from G_b and tau (one warp per block): column i of T is formed after
-// columns 0..i-1; lane r < i forms T[r][i]
+// T_b from G_b and tau (one warp per block): G_b and the block's tau are staged
+// in shared memory, then column i of T is formed after columns 0..i-1; lane
+// r < i forms T[r][i]
 __global__ void qr_wy_t_kernel(const double2* tau, int n, const double2* G, double2* Tf) {
   __shared__ double2 T[WY_NB][WY_NB];
+  __shared__ double2 Gs[WY_NB][WY_NB];
+  __shared__ double2 ts[WY_NB];
   const int b = blockIdx.x, j0 = b * WY_NB, nbk = min(WY_NB, n - j0);
   const int lane = threadIdx.x;
   const double2* Gb = G + (size_t)b * WY_NB * WY_NB;
+  for (int e = lane; e < WY_NB * WY_NB; e += 32) {
+    const int r = e / WY_NB, c = e % WY_NB;
+    Gs[r][c] = r < c && c < nbk ? Gb[e] : make_double2(0.0, 0.0);  // only the strict upper part is formed
+  }
+  if (lane < nbk) ts[lane] = tau[j0 + lane];
+  __syncwarp();
   for (int i = 0; i < nbk; ++i) {
-    const double2 ti = tau[j0 + i];
+    const double2 ti = ts[i];
     double2 t = make_double2(0.0, 0.0);
     if (lane < i) {
       // sum_{k = lane}^{i-1} T[lane][k] G[k][i] (T upper triangular)
-      for (int k = lane; k < i; ++k) t = cfma(T[lane][k], Gb[k * WY_NB + i], t);
+      for (int k = lane; k < i; ++k) t = cfma(T[lane][k], Gs[k][i], t);
       t = cmul(make_double2(-ti.x, -ti.y), t);
     } else if (lane == i) {
       t = ti;
@@ -826,6 +837,157 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// One-sided (Hestenes) Jacobi on the columns of an M x N complex matrix
+// (column-major, ld = M, N even): rotations of column pairs until every pair
+// is orthogonal to |x^H y| <= tol sqrt(|x|^2 |y|^2); the columns then are the
+// left singular vectors scaled by the singular values. One cooperative launch:
+// each round takes N/2 disjoint pairs (the circle ordering: position 0 fixed,
+// the others rotating, so every pair meets once per sweep of N - 1 rounds),
+// CTA c the pairs c, c + G, ...; the rounds are separated by a grid barrier on
+// a global counter (bounded wait, err code 10). A sweep without any rotation
+// ends the loop (a vote in votes[sweep], zeroed before the launch).
+//
+// For columns x, y with a = |x|^2, b = |y|^2, c = x^H y = |c| w:
+// zeta = (b - a) / (2|c|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+// cs = 1 / sqrt(1 + t^2), sn = cs t, and
+// x' = cs x - sn conj(w) y,  y' = sn w x + cs y   (x'^H y' = 0).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int jac_pos(int j, int r, int N) {
+  return j == 0 ? 0 : 1 + (j - 1 + r) % (N - 1);
+}
+
+__device__ bool jac_barrier(unsigned int* bar, unsigned int target, int* err) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    if (ld_acquire(reinterpret_cast<const int*>(bar)) < (int)target) {
+      const unsigned long long t0 = qr_gtimer();
+      while (ld_acquire(reinterpret_cast<const int*>(bar)) < (int)target) {
+        if (qr_gtimer() - t0 > QR_WAIT_NS) {
+          atomicExch(err, 10);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(256) jacobi_cols_kernel(double2* A, int M, int N, int maxsweeps, double tol,
+                                                          const double* frob2, unsigned int* bar, int* votes,
+                                                          int* err) {
+  __shared__ double red[4][8];
+  __shared__ double sc[4];
+  const int G = gridDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // columns below 2^-50 of the matrix's Frobenius norm are rounding residue
+  // (rank deficiency): they are not rotated
+  const double small = *frob2 * 7.888609052210118e-31;  // 2^-100
+  unsigned int nbar = 0;
+  for (int sweep = 0; sweep < maxsweeps; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < N - 1; ++r) {
+      for (int pi = blockIdx.x; pi < N / 2; pi += G) {
+        const int u = jac_pos(pi, r, N), v = jac_pos(N - 1 - pi, r, N);
+        const int p = min(u, v), q = max(u, v);
+        double2* x = A + (long long)p * M;
+        double2* y = A + (long long)q * M;
+        double sa = 0.0, sb = 0.0, cr = 0.0, ci = 0.0;
+        for (int i = threadIdx.x; i < M; i += blockDim.x) {
+          const double2 xi = __ldcg(x + i), yi = __ldcg(y + i);
+          sa = fma(xi.x, xi.x, fma(xi.y, xi.y, sa));
+          sb = fma(yi.x, yi.x, fma(yi.y, yi.y, sb));
+          cr = fma(xi.x, yi.x, fma(xi.y, yi.y, cr));   // Re conj(x) y
+          ci = fma(xi.x, yi.y, fma(-xi.y, yi.x, ci));  // Im conj(x) y
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          sa += __shfl_xor_sync(0xffffffffu, sa, o);
+          sb += __shfl_xor_sync(0xffffffffu, sb, o);
+          cr += __shfl_xor_sync(0xffffffffu, cr, o);
+          ci += __shfl_xor_sync(0xffffffffu, ci, o);
+        }
+        if (lane == 0) {
+          red[0][wid] = sa;
+          red[1][wid] = sb;
+          red[2][wid] = cr;
+          red[3][wid] = ci;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+          double t = 0.0;
+          for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];  // fixed order
+          sc[threadIdx.x] = t;
+        }
+        __syncthreads();
+        const double a = sc[0], b = sc[1], c_re = sc[2], c_im = sc[3];
+        const double g = sqrt(c_re * c_re + c_im * c_im);
+        if (a > small && b > small && g > tol * sqrt(a) * sqrt(b)) {
+          rotated = 1;
+          const double zeta = (b - a) / (2.0 * g);
+          const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
+                                              : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          const double wr = c_re / g, wi = c_im / g;  // w = c / |c|
+          for (int i = threadIdx.x; i < M; i += blockDim.x) {
+            const double2 xi = __ldcg(x + i), yi = __ldcg(y + i);
+            // conj(w) y = (wr yr + wi yi, wr yi - wi yr);  w x = (wr xr - wi xi, wr xi + wi xr)
+            const double2 cy = make_double2(wr * yi.x + wi * yi.y, wr * yi.y - wi * yi.x);
+            const double2 wx = make_double2(wr * xi.x - wi * xi.y, wr * xi.y + wi * xi.x);
+            __stcg(x + i, make_double2(cs * xi.x - sn * cy.x, cs * xi.y - sn * cy.y));
+            __stcg(y + i, make_double2(sn * wx.x + cs * yi.x, sn * wx.y + cs * yi.y));
+          }
+        }
+        __syncthreads();
+      }
+      if (!jac_barrier(bar, (++nbar) * (unsigned int)G, err)) return;
+    }
+    if (threadIdx.x == 0 && rotated) atomicOr(votes + sweep, 1);
+    if (!jac_barrier(bar, (++nbar) * (unsigned int)G, err)) return;
+    if (ld_acquire(votes + sweep) == 0) return;  // every CTA reads the same settled vote
+  }
+}
+
+// squared norms of the N columns (a warp per column)
+__global__ void col_norms_kernel(const double2* A, int M, int N, double* nrm) {
+  const int lane = threadIdx.x & 31;
+  for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < N; c += gridDim.x * (blockDim.x >> 5)) {
+    double s = 0.0;
+    for (int i = lane; i < M; i += 32) {
+      const double2 v = A[(long long)c * M + i];
+      s = fma(v.x, v.x, fma(v.y, v.y, s));
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) nrm[c] = s;
+  }
+}
+
+// column j goes to output column rank(j) when rank(j) < k, rank = the number
+// of columns with a larger norm (ties: lower index first): the k columns of
+// largest norm in decreasing order
+__global__ void gather_top_kernel(const double2* A, int M, int N, const double* nrm, int k, double2* out) {
+  const int j = blockIdx.x;
+  __shared__ int s_rank;
+  if (threadIdx.x == 0) s_rank = 0;
+  __syncthreads();
+  const double nj = nrm[j];
+  int cnt = 0;
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    const double nc = nrm[c];
+    cnt += (nc > nj || (nc == nj && c < j)) ? 1 : 0;
+  }
+  atomicAdd(&s_rank, cnt);
+  __syncthreads();
+  const int rk = s_rank;
+  if (rk >= k) return;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) out[(long long)rk * M + i] = A[(long long)j * M + i];
+}
+
 __global__ void qr_extract_r_kernel(const double2* A, const double2* beta, int m, int n, double2* R) {
   long long total = (long long)n * n;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -927,11 +1089,47 @@ int qr64_form_q(const Launch& L, const z64* V_, const z64* tau_, int m, int n, z
   if (nblk > 65535) return TEVO_ESHAPE;
   qr_wy_gram_kernel<<<dim3(nblk, WY_GRAM_SPLIT), 256, 0, L.stream>>>(V, m, n, G);
   qr_wy_t_kernel<<<nblk, 32, 0, L.stream>>>(tau, n, G, Tf);
-  qr_wy_form_kernel<<<n, 256, smem, L.stream>>>(V, m, n, Tf, reinterpret_cast<double2*>(Q), sQr, sQc,
+  qr_wy_form_kernel<<<n, 512, smem, L.stream>>>(V, m, n, Tf, reinterpret_cast<double2*>(Q), sQr, sQc,
                                                 std::min(n, L.num_sms));
   *L.launches += 3;
   if (L.prof) L.prof->end(L.stream, pr);
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int jacobi_top_columns(const Launch& L, z64* A_, int M, int N, int k, z64* out, void* ws, int* err) {
+  if (M < 1 || N < 2 || (N & 1) || k < 1 || k > N) return TEVO_ESHAPE;
+  double2* A = reinterpret_cast<double2*>(A_);
+  unsigned int* bar = static_cast<unsigned int*>(ws);
+  int* votes = reinterpret_cast<int*>(bar + 64);
+  double* frob2 = reinterpret_cast<double*>(votes + JAC_MAX_SWEEPS + 64);
+  double* part = frob2 + 8;
+  double* nrm = part + FROB_BLOCKS;
+  if (cudaMemsetAsync(ws, 0, sizeof(unsigned int) * (64 + JAC_MAX_SWEEPS + 64), L.stream) != cudaSuccess)
+    return TEVO_ECUDA;
+  int G = std::min(N / 2, L.num_sms);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_cols_kernel, 256, 0) != cudaSuccess ||
+      per_sm * L.num_sms < G)
+    return TEVO_EUNSUPPORTED;
+  frob_partial_kernel<<<FROB_BLOCKS, 256, 0, L.stream>>>(A, (long long)M * N, part);
+  sum_partials_kernel<<<1, 256, 0, L.stream>>>(part, FROB_BLOCKS, frob2);
+  *L.launches += 2;
+  int maxsw = JAC_MAX_SWEEPS;
+  // pairs count as orthogonal below a few roundings of an M-term dot product
+  double tol = std::max(JAC_TOL, 2.0 * std::sqrt((double)M) * 2.220446049250313e-16);
+  const double* f2 = frob2;
+  void* args[] = {&A, &M, &N, &maxsw, &tol, &f2, &bar, &votes, &err};
+  if (cudaLaunchCooperativeKernel((void*)jacobi_cols_kernel, dim3(G), dim3(256), args, 0, L.stream) != cudaSuccess)
+    return TEVO_ECUDA;
+  const int nb = std::max(1, std::min((N * 32 + 255) / 256, 8 * L.num_sms));
+  col_norms_kernel<<<nb, 256, 0, L.stream>>>(A, M, N, nrm);
+  gather_top_kernel<<<N, 256, 0, L.stream>>>(A, M, N, nrm, k, reinterpret_cast<double2*>(out));
+  *L.launches += 3;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+size_t jacobi_ws_bytes(int N) {
+  return sizeof(unsigned int) * (64 + JAC_MAX_SWEEPS + 64) + sizeof(double) * (8 + FROB_BLOCKS + N + 64);
 }
 
 int qr64_extract_r(const Launch& L, const z64* A, const z64* beta, int m, int n, z64* R) {
@@ -976,6 +1174,13 @@ __global__ void fill_kernel(double2* dst, long long n, double re, double im) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x)
     dst[idx] = make_double2(re, im);
+}
+
+__global__ void eye_kernel(double2* dst, int n) {
+  const long long total = (long long)n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x)
+    dst[idx] = make_double2(idx / n == idx % n ? 1.0 : 0.0, 0.0);
 }
 
 __global__ void normalize_kernel(double2* x, long long n, const double* nrm2, double* lognorm, int* flag) {
@@ -1063,6 +1268,13 @@ int fill64(const Launch& L, z64* dst, size_t n, double re, double im) {
   if (n == 0) return 0;
   fill_kernel<<<grid_for((long long)n, L.num_sms), 256, 0, L.stream>>>(reinterpret_cast<double2*>(dst),
                                                                        (long long)n, re, im);
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int eye64(const Launch& L, z64* dst, int n) {
+  if (n <= 0) return 0;
+  eye_kernel<<<grid_for((long long)n * n, L.num_sms), 256, 0, L.stream>>>(reinterpret_cast<double2*>(dst), n);
   ++*L.launches;
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
 }

@@ -127,6 +127,13 @@ int qr64_factor_coop(const Launch& L, z64* A, int m, int n, z64* V, z64* tau, z6
 size_t qr64_wy_bytes(int n);
 int qr64_form_q(const Launch& L, const z64* V, const z64* tau, int m, int n, z64* Q, long long sQr,
                 long long sQc, void* wy);
+// one-sided Jacobi on the columns of the M x N column-major A (N even; A is
+// overwritten), then the k columns of largest norm copied to out (M x k,
+// column-major) in decreasing order of norm: the leading left singular vectors
+// of A, each scaled by its singular value. ws: jacobi_ws_bytes(N) bytes;
+// a grid barrier that gives up sets *err (code 10).
+size_t jacobi_ws_bytes(int N);
+int jacobi_top_columns(const Launch& L, z64* A, int M, int N, int k, z64* out, void* ws, int* err);
 // R (n x n) from the factored A and beta: dense upper-triangular, row-major
 int qr64_extract_r(const Launch& L, const z64* A, const z64* beta, int m, int n, z64* R);
 
@@ -136,6 +143,8 @@ int mirror_site64(const Launch& L, const z64* in, z64* out, int na, int d, int n
 int copy2d64(const Launch& L, const z64* src, long long sr, long long sc, z64* dst, long long dr,
              long long dc, int rows, int cols);
 int fill64(const Launch& L, z64* dst, size_t n, double re, double im);
+// dst = the n x n identity (complex, row-major)
+int eye64(const Launch& L, z64* dst, int n);
 // sum |x|^2 over n entries into *out (device), deterministic two-pass
 int norm2_64(const Launch& L, const z64* x, size_t n, double* out, double* scratch);
 // x /= sqrt(*nrm2); *lognorm += log(sqrt(*nrm2)); flags nonfinite into *flag

@@ -165,6 +165,10 @@ def test_probe_cases_issue_their_calls(monkeypatch, capsys):
         "tc": [("init", 256), ("step", 1, 0x103), ("init", 256), ("step", 1, 0x102)],
         "qr": [("init", 256)] + [("step", 2, 0x200)] * 5,
     }
+    fake.TWO_SITE = 0x400
+    fake.evolve_step_batched = lambda psis, Ws, sweeps, prec: calls.append(("batched", len(psis), sweeps, prec))
+    expect["batched"] = [("init", c["D"]) for c in bench.wl.batched_chains()[:8]] + [("batched", 8, 1, 0x102)] * 3
+    expect["twosite"] = [("init", 64), ("step", 1, 0x400)]
     for case in bench.PROBES:
         calls.clear()
         bench.probe(SimpleNamespace(probe=case, probe_L=20, probe_sweeps=1))

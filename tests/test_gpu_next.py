@@ -73,3 +73,124 @@ def test_imaginary_time_reaches_ground_state(ctx):
     gs = U[:, 0]
     exact = dense.expect_dense(gs, [X], L).real
     assert np.abs(tv.measure_local(psi, [X]).real - exact).max() < 1e-3
+
+
+@pytest.mark.parametrize("N", [1, 3])
+def test_thermal_state_by_purification(ctx, N):
+    """Finite-temperature state of the TFI chain (L = 6, g = 1.05, beta = 1) by
+    purification: each site carries a physical spin and an ancilla (d = 4), the
+    MPO acts on the physical legs (blocks O (x) 1), the start is the product of
+    maximally entangled pairs, and n = 10 steps of real tau = -beta / 20 give
+    e^{-beta H} after tracing the ancillas. The GPU's fp64 form equals the
+    oracle doing the same (1e-10) and the Gibbs averages from eigh within the
+    order-N MPO's error (as the oracle's pin bounds it)."""
+    L, beta, n, D = 6, 1.0, 10, 64
+    blocks = wl.purify_blocks(*wl.tfi_blocks(L, 1.05))
+    tau = -beta / (2 * n)
+    W = tv.mpo_build(ctx, *blocks, N, tau)
+    Wo = mpo.build_mpo(*blocks, N, tau)
+    v0 = wl.purified_infinite_temperature(L, 2)
+    psi = tv.mps_init(ctx, v0, D)
+    ref = fit.product_mps(v0, D)
+    X, _, Z = wl.pauli()
+    ops = [wl.purify_op(X), wl.purify_op(Z)]
+    for k in range(n):
+        tv.evolve_step(psi, W, tau, D, 2, tv.FP64)
+        ref, _ = fit.evolve_step(ref, Wo, 2, canonical=k > 0)
+    got = tv.measure_local(psi, ops).real
+    assert np.abs(got - fit.measure_local(ref, ops).real).max() < 1e-10
+    exact = dense.thermal_expect(dense.hamiltonian_from_blocks(*wl.tfi_blocks(L, 1.05)), beta, [X, Z], L).real
+    assert np.abs(got - exact).max() < (5e-3 if N == 1 else 2e-5)
+
+
+def test_splitting_against_native_second_order(ctx):
+    """Sec. 8.3's comparison on the XXZ chain (L = 10, Neel, D = 32, t = 2): two
+    first-order MPOs at tau (1 +- i)/2 (bond 1 + chi = 4 each) against the
+    native second-order MPO (bond 1 + chi + chi^2 = 13). On the GPU both equal
+    the oracle doing the same (1e-10) and both errors against exact evolution
+    fall by about 4 when the step halves; the split's error is within 1.5x the
+    native one (the oracle measures 1.15-1.2x)."""
+    L, D = 10, 32
+    blocks = wl.xxz_blocks(L, 0.5)
+    H = dense.hamiltonian_from_blocks(*blocks)
+    X, _, Z = wl.pauli()
+    v0 = wl.product_state("neel", L)
+    res = {}
+    for t in (0.2, 0.1):
+        tau = -1j * t
+        taus = (tau * (1 + 1j) / 2, tau * (1 - 1j) / 2)
+        n = int(round(2 / t))
+        W2 = tv.mpo_build(ctx, *blocks, 2, tau)
+        W1 = [tv.mpo_build(ctx, *blocks, 1, s) for s in taus]
+        assert W2.bond_dims()[L // 2] == 13 and W1[0].bond_dims()[L // 2] == 4
+        a, b = tv.mps_init(ctx, v0, D), tv.mps_init(ctx, v0, D)
+        ao, bo = fit.product_mps(v0, D), fit.product_mps(v0, D)
+        W2o = mpo.build_mpo(*blocks, 2, tau)
+        W1o = [mpo.build_mpo(*blocks, 1, s) for s in taus]
+        for k in range(n):
+            tv.evolve_step(a, W2, tau, D, 2, tv.FP64)
+            ao, _ = fit.evolve_step(ao, W2o, 2, canonical=k > 0)
+            for j in (0, 1):
+                tv.evolve_step(b, W1[j], taus[j], D, 2, tv.FP64)
+                bo, _ = fit.evolve_step(bo, W1o[j], 2, canonical=k > 0 or j > 0)
+        ga, gb = tv.measure_local(a, [X, Z]).real, tv.measure_local(b, [X, Z]).real
+        assert np.abs(ga - fit.measure_local(ao, [X, Z]).real).max() < 1e-10
+        assert np.abs(gb - fit.measure_local(bo, [X, Z]).real).max() < 1e-10
+        v = dense.product_vector(v0)
+        E = dense.expm_tau_h(H, tau)
+        for _ in range(n):
+            v = E @ v
+        ex = dense.expect_dense(v, [X, Z], L).real
+        res[t] = (np.abs(ga - ex).max(), np.abs(gb - ex).max())
+    print("native W2 / split errors at t = 2:", {t: (f"{a:.2e}", f"{b:.2e}") for t, (a, b) in res.items()})
+    for k in (0, 1):
+        assert 3.0 < res[0.2][k] / res[0.1][k] < 5.0
+    assert res[0.1][1] < 1.5 * res[0.1][0]
+
+
+def test_cylinder_quench_against_oracle(ctx):
+    """The efficiency workload of Sec. 8.2 at a size the oracle runs: the 2-D TFI
+    cylinder (circumference 4, spiral boundary conditions, length 3, L = 12,
+    g = 3.5), a ground state by 20 imaginary-time steps from a seeded random
+    state, the middle spin flipped on the host, 5 real-time steps of order 2:
+    the GPU's observables and the magnitude of its overlap with the ground state
+    equal the oracle's (1e-10). (From a product state the two drift apart by
+    about 1e-10 per 20 steps: the fit's directions of rounding-level weight.)"""
+    Lx, Wc, g, D = 3, 4, 3.5, 16
+    L = Lx * Wc
+    blocks = wl.tfi_cylinder_blocks(Lx, Wc, g)
+    X, _, Z = wl.pauli()
+    plus = np.tile(np.array([1.0, 1.0], np.complex128) / np.sqrt(2), (L, 1))
+    Wi, Wio = tv.mpo_build(ctx, *blocks, 3, -0.1), mpo.build_mpo(*blocks, 3, -0.1)
+    # imaginary time from a seeded random (full-rank) state: no bond starts
+    # rank-deficient, so no rounding-decided directions enter the fit
+    start = wl.random_mps(L, 2, D, seed=9)
+    psi = tv.mps_init(ctx, plus, D)
+    for i in range(L):
+        psi.set_site(i, start[i])
+    ref = [x.copy() for x in start]
+    for k in range(20):
+        tv.evolve_step(psi, Wi, -0.1, D, 2, tv.FP64)
+        ref, _ = fit.evolve_step(ref, Wio, 2, canonical=k > 0)
+    e_gs = np.abs(tv.measure_local(psi, [X, Z]).real - fit.measure_local(ref, [X, Z]).real).max()
+    gs_sites = [psi.site(i) for i in range(L)]
+    gs = tv.mps_init(ctx, plus, D)
+    for i in range(L):
+        gs.set_site(i, gs_sites[i])
+    gs_o = [x.copy() for x in ref]
+    a = psi.site(L // 2)
+    psi.set_site(L // 2, np.einsum("st,atb->asb", X, a))
+    ref[L // 2] = np.einsum("st,atb->asb", X, ref[L // 2])
+    tau = -0.1j
+    Wr, Wro = tv.mpo_build(ctx, *blocks, 2, tau), mpo.build_mpo(*blocks, 2, tau)
+    for k in range(5):
+        tv.evolve_step(psi, Wr, tau, D, 2, tv.FP64)
+        ref, _ = fit.evolve_step(ref, Wro, 2, canonical=False if k == 0 else True)
+    e_q = np.abs(tv.measure_local(psi, [X, Z]).real - fit.measure_local(ref, [X, Z]).real).max()
+    print(f"cylinder: ground state {e_gs:.1e}, after the quench {e_q:.1e}")
+    assert e_gs < 1e-10 and e_q < 1e-10
+    # |<gs|psi>| (the global phase of a fitted state is a gauge choice that
+    # rounding can decide after a product-state start)
+    la, _ = tv.mps_overlap(gs, psi)
+    la_o, _ = fit.overlap(gs_o, ref)
+    assert abs(la - la_o) < 1e-10

@@ -24,6 +24,7 @@ __all__ = [
     "pauli", "spin_half", "spin_one", "tfi_blocks", "xxz_blocks", "lr_ising_blocks",
     "spin1_blocks", "random_blocks", "product_state", "random_product_vectors",
     "random_mps", "bond_dims", "LR_A", "LR_B", "CONFIGS", "config", "batched_chains",
+    "purify_blocks", "purify_op", "purified_infinite_temperature", "tfi_cylinder_blocks",
 ]
 
 # ----------------------------------------------------------------------------
@@ -108,6 +109,29 @@ def lr_ising_blocks(L, g, a=LR_A, b=LR_B):
     return _stack(L, A1, B1, C1, -g * X)
 
 
+def tfi_cylinder_blocks(Lx, Wc, g, J=1.0):
+    """Transverse-field Ising model on a cylinder of circumference Wc and length
+    Lx with spiral boundary conditions (Sec. 2.4, the 2-D example): the sites
+    are numbered along a helix, i = 0 .. Wc Lx - 1, and site i couples to i + 1
+    (around the cylinder) and to i + Wc (along it),
+        H = -J sum_i (Z_i Z_{i+1} + Z_i Z_{i+Wc}) - g sum_i X_i
+    (bonds that would leave the chain are absent). As an MPO the middle level is
+    a shift register of Wc places (chi = Wc): C puts -J Z in place 0, A moves
+    place k to k + 1, B closes a bond from place 0 (range 1) and from place
+    Wc - 1 (range Wc)."""
+    X, _, Z = pauli()
+    L = Wc * Lx
+    A1 = np.zeros((Wc, Wc, 2, 2), np.complex128)
+    for k in range(Wc - 1):
+        A1[k, k + 1] = np.eye(2)
+    B1 = np.zeros((Wc, 2, 2), np.complex128)
+    B1[0] = Z
+    B1[Wc - 1] = B1[Wc - 1] + Z
+    C1 = np.zeros((Wc, 2, 2), np.complex128)
+    C1[0] = -J * Z
+    return _stack(L, A1, B1, C1, -g * X)
+
+
 def spin1_blocks(L, J=1.0, Dz=0.3):
     """H = J sum_i S_i . S_{i+1} + Dz sum_i (Sz_i)^2 for spin 1 (chi = 3, d = 3)."""
     Sx, Sy, Sz = spin_one()
@@ -135,6 +159,24 @@ def random_blocks(L, chi, d, seed, scale=1.0, a_scale=0.5, uniform=True):
     return A, B, C, D
 
 
+def purify_op(O):
+    """O acting on the physical leg of a (physical, ancilla) pair: O (x) 1."""
+    return np.kron(O, np.eye(O.shape[-1], dtype=np.complex128))
+
+
+def purify_blocks(A, B, C, D):
+    """Hamiltonian blocks on the doubled site (physical (x) ancilla, dimension
+    d^2): every operator entry O becomes O (x) 1, so the MPO acts on the
+    physical legs only (the purification of a thermal state)."""
+    def lift(X):
+        d = X.shape[-1]
+        out = np.zeros(X.shape[:-2] + (d * d, d * d), np.complex128)
+        for idx in np.ndindex(*X.shape[:-2]):
+            out[idx] = purify_op(X[idx])
+        return out
+    return lift(A), lift(B), lift(C), lift(D)
+
+
 # ----------------------------------------------------------------------------
 # states
 # ----------------------------------------------------------------------------
@@ -158,6 +200,16 @@ def product_state(kind, L, d=2):
             v[i, i % 2] = 1
     else:
         raise ValueError(kind)
+    return v
+
+
+def purified_infinite_temperature(L, d):
+    """Site vectors [L, d^2] of the product of maximally entangled
+    (physical, ancilla) pairs sum_s |s>|s> / sqrt(d): tracing out the ancillas
+    leaves the infinite-temperature state 1/d^L."""
+    v = np.zeros((L, d * d), np.complex128)
+    for s in range(d):
+        v[:, s * d + s] = 1.0 / np.sqrt(d)
     return v
 
 
