@@ -32,10 +32,14 @@
 //
 // The tensor-core schedule is that of the plain complex GEMM (k_tc.cu): a
 // persistent CTA per SM, a TMA producer warp, one thread issuing tcgen05.mma,
-// eight epilogue warps (two per tensor-memory lane quarter), two tensor-memory accumulator buffers (a pass drains
-// while the next accumulates). A stage holds the (re, im) planes of one A slice
-// and of one B slice for 32 K-indices; it feeds four real MMAs per 16 K:
-//   Re += Ar Br - Ai Bi,   Im += Ar Bi + Ai Br.
+// eight epilogue warps (two per tensor-memory lane quarter), two tensor-memory
+// accumulator buffers (a pass drains while the next accumulates). A stage holds
+// the (re, im) planes of one A slice and the (-im, re, im) planes of one B slice
+// for 32 K-indices. The accumulator of a 128 x 128 complex tile is one
+// 128 x 256 fp32 block, Re in columns 0..127 and Im in 128..255, and each 16 K
+// take two real MMAs of N = 256 whose B operands are two consecutive planes:
+//   [Re | Im] += Ar [Br ; Bi]  and  [Re | Im] += Ai [-Bi ; Br].
+// (Four N = 128 MMAs per 16 K ran the tensor pipe about 1.5x slower.)
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -65,9 +69,11 @@ constexpr int OZ_LO_SHIFT = OZ_W * OZ_HI_GROUPS;
 constexpr int OZ_TM = 128, OZ_TN = 128;
 constexpr int OZ_KCB = 64;                 // bytes of K per stage row (32 bf16)
 constexpr int OZ_KT_CHUNK = 8;             // K-tiles of 32 per exact chunk: 256 K-indices
-constexpr int OZ_NSTAGE = 6;
-constexpr int OZ_A_BYTES = 2 * OZ_TM * OZ_KCB;  // re, im planes of one slice: 16 KB
-constexpr int OZ_B_BYTES = 2 * OZ_TN * OZ_KCB;
+constexpr int OZ_NSTAGE = 5;
+constexpr int OZ_A_PLANES = 2;                  // per A slice: re, im
+constexpr int OZ_B_PLANES = 3;                  // per B slice: -im, re, im
+constexpr int OZ_A_BYTES = OZ_A_PLANES * OZ_TM * OZ_KCB;  // 16 KB
+constexpr int OZ_B_BYTES = OZ_B_PLANES * OZ_TN * OZ_KCB;  // 24 KB
 constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
 constexpr int OZ_SMEM_BYTES = OZ_NSTAGE * OZ_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 #ifndef OZ_EPILOGUE_WARPS
@@ -80,7 +86,8 @@ static_assert(OZ_EPI_WARPS == 4 || OZ_EPI_WARPS == 8, "epilogue warps");
 constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
 // one operand to cut into digit slices: element (r, k) of R x K at
 // src[(r / R2) * sR1 + (r % R2) * sR + k * sK] (conjugated when conj), digit
-// planes written to dst[p * plane_stride + r * row_pitch + k], the row maxima
+// planes written to dst[p * plane_stride + r * row_pitch + k] (planes per
+// slice: 2 = re, im; 3 = -im, re, im), the row maxima
 // of the entries' exponent bounds to rowexp[r] (set to OZ_NONE before), the
 // row exponents to exps[r]
 struct OzSplit {
@@ -95,6 +102,7 @@ struct OzSplit {
   int* rowexp;
   int R2;
   long long sR1;
+  int planes;
 };
 
 __device__ __forceinline__ long long row_offset(const OzSplit& o, long long r) {
@@ -331,8 +339,8 @@ __device__ __forceinline__ int digit_of(unsigned long long U, int s, int G) {
   return d < -(1 << OZ_P) ? -(1 << OZ_P) : d;
 }
 
-// digit planes [2G][R][row_pitch] (plane 2s = Re of slice s, 2s+1 = Im) of a
-// 32-row x 64-K tile, staged in shared memory so that the fp64 reads (along the
+// digit planes [planes G][R][row_pitch] (planes = 2: plane 2s = Re of slice s,
+// 2s+1 = Im; planes = 3: 3s = -Im, 3s+1 = Re, 3s+2 = Im) of a 32-row x 64-K tile, staged in shared memory so that the fp64 reads (along the
 // contiguous source index) are coalesced; each thread then forms the digits of
 // two neighbouring K entries and writes them as one 4-byte bf16 pair per plane
 template <bool ROWS_CONTIG>
@@ -384,10 +392,20 @@ __global__ void oz_slice_kernel(OzSplit o) {
       __nv_bfloat162 re, im;
       re.x = digit_bf16[digit_of(u0r, s, o.G) + H];
       re.y = digit_bf16[digit_of(u1r, s, o.G) + H];
-      im.x = digit_bf16[digit_of(u0i, s, o.G) + H];
-      im.y = digit_bf16[digit_of(u1i, s, o.G) + H];
-      dst[(long long)(2 * s) * ps2] = re;
-      dst[(long long)(2 * s + 1) * ps2] = im;
+      const int d0i = digit_of(u0i, s, o.G), d1i = digit_of(u1i, s, o.G);
+      im.x = digit_bf16[d0i + H];
+      im.y = digit_bf16[d1i + H];
+      if (o.planes == 3) {
+        __nv_bfloat162 nim;
+        nim.x = digit_bf16[H - d0i];
+        nim.y = digit_bf16[H - d1i];
+        dst[(long long)(3 * s) * ps2] = nim;
+        dst[(long long)(3 * s + 1) * ps2] = re;
+        dst[(long long)(3 * s + 2) * ps2] = im;
+      } else {
+        dst[(long long)(2 * s) * ps2] = re;
+        dst[(long long)(2 * s + 1) * ps2] = im;
+      }
     }
   }
 }
@@ -490,8 +508,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 const uint32_t fb = full0 + 8 * st;
                 mbar_expect_tx(fb, OZ_STAGE_BYTES);
                 uint8_t* sp = smem + st * OZ_STAGE_BYTES;
-                tma_load_4d(smem_u32(sp), &tmA, kt * 32, 0, m0, 2 * s, fb);
-                tma_load_4d(smem_u32(sp + OZ_A_BYTES), &tmB, kt * 32, 0, n0, 2 * (g - s), fb);
+                tma_load_4d(smem_u32(sp), &tmA, kt * 32, 0, m0, OZ_A_PLANES * s, fb);
+                tma_load_4d(smem_u32(sp + OZ_A_BYTES), &tmB, kt * 32, 0, n0, OZ_B_PLANES * (g - s), fb);
               }
       }
       // do not leave while copies are in flight
@@ -500,10 +518,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // instruction descriptor: fp32 accumulate, bf16 A and B, K-major, M = 128, N = 128
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) |
+      // instruction descriptor: fp32 accumulate, bf16 A and B, K-major, M = 128,
+      // N = 256 (the Re and Im column halves of the tile's accumulator)
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * OZ_TN) >> 3) << 17) |
                              ((uint32_t)(OZ_TM >> 4) << 24);
-      const uint32_t neg = 1u << 13;  // negate A
       const uint64_t plane_a = (uint64_t)((OZ_TM * OZ_KCB) >> 4), plane_b = (uint64_t)((OZ_TN * OZ_KCB) >> 4);
       long long q = 0;
       int i = 0;  // pass counter
@@ -522,7 +540,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t dre = tmem + (uint32_t)(b * 2 * OZ_TN), dim = dre + OZ_TN;
+            const uint32_t dacc = tmem + (uint32_t)(b * 2 * OZ_TN);  // [Re | Im], 256 columns
             bool first = true;
             for (int kt = kt0; kt < kt1 && ok; ++kt)
               for (int s = 0; s <= g; ++s, ++q) {
@@ -533,15 +551,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t sa = smem_u32(smem + st * OZ_STAGE_BYTES);
-                const uint64_t ar = sdesc(sa), br = sdesc(sa + OZ_A_BYTES);
+                // B planes in the stage: 0 = -Bi, 1 = Br, 2 = Bi
+                const uint64_t ar = sdesc(sa), bn = sdesc(sa + OZ_A_BYTES);
 #pragma unroll
                 for (int ks = 0; ks < OZ_KCB / 32; ++ks) {
                   const uint64_t o = (uint64_t)((ks * 32) >> 4);
                   const uint32_t acc = first ? 0u : 1u;
-                  mma<TC_BF16>(dre, ar + o, br + o, idesc, acc);                       // Re  = Ar Br
-                  mma<TC_BF16>(dre, ar + plane_a + o, br + plane_b + o, idesc | neg, 1u);  // Re -= Ai Bi
-                  mma<TC_BF16>(dim, ar + o, br + plane_b + o, idesc, acc);             // Im  = Ar Bi
-                  mma<TC_BF16>(dim, ar + plane_a + o, br + o, idesc, 1u);              // Im += Ai Br
+                  mma<TC_BF16>(dacc, ar + o, bn + plane_b + o, idesc, acc);  // [Re | Im]  = Ar [Br ; Bi]
+                  mma<TC_BF16>(dacc, ar + plane_a + o, bn + o, idesc, 1u);   // [Re | Im] += Ai [-Bi ; Br]
                   first = false;
                 }
                 mma_commit(empty0 + 8 * st);
@@ -669,8 +686,8 @@ OzPlan plan(int M, int N, int K, int G, int num_sms) {
   p.cps = (p.nchunks + splits - 1) / splits;
   p.splits = (p.nchunks + p.cps - 1) / p.cps;
   const long long kp = pad8(K);
-  p.a_bytes = al256((size_t)2 * G * M * kp * 2);
-  p.b_bytes = al256((size_t)2 * G * N * kp * 2);
+  p.a_bytes = al256((size_t)OZ_A_PLANES * G * M * kp * 2);
+  p.b_bytes = al256((size_t)OZ_B_PLANES * G * N * kp * 2);
   p.e_bytes = al256((size_t)(M + N) * 2 * sizeof(int));
   p.p_bytes = p.splits > 1 ? al256((size_t)p.splits * M * N * 16) : 0;
   // persistent grid: one CTA per SM at most
@@ -749,23 +766,23 @@ int ozgemm64(const Launch& L, const GemmDesc& g, int slices, void* ws, size_t ws
   const long long kp = pad8(g.K);
   // A(m, k) at A + m sAm + k sAk; B(k, n) at B + k sBk + n sBn, read as rows n
   OzSplit sa{static_cast<const double2*>(g.A), g.sAm, g.sAk, g.M, g.K, g.conjA, slices, da, (long long)g.M * kp, kp,
-             ea, mxa, g.M, 0};
+             ea, mxa, g.M, 0, OZ_A_PLANES};
   // rows of B: (batch b, n) at b sBb + n sBn
   OzSplit sb{static_cast<const double2*>(g.B), g.sBn, g.sBk, Nt, g.K, 0, slices, db, (long long)Nt * kp, kp, eb,
-             mxb, g.N, g.sBb};
+             mxb, g.N, g.sBb, OZ_B_PLANES};
   const int pr_split = L.prof ? L.prof->begin(L.stream, TEVO_PROF_OZSPLIT, 0.0,
-                                              (16.0 + 4.0 * slices) * ((double)g.M + Nt) * g.K)
+                                              ((16.0 + 4.0 * slices) * g.M + (16.0 + 6.0 * slices) * Nt) * g.K)
                               : -1;
   int e = split_operand(L, sa);
   if (!e) e = split_operand(L, sb);
   if (L.prof) L.prof->end(L.stream, pr_split);
   if (e) return e;
 
-  TcOperand oa{da, 2, 2 * slices, (long long)g.M * kp, g.M, kp, g.K, 1, kp};
-  TcOperand ob{db, 2, 2 * slices, (long long)Nt * kp, Nt, kp, g.K, 1, kp};
+  TcOperand oa{da, 2, OZ_A_PLANES * slices, (long long)g.M * kp, g.M, kp, g.K, 1, kp};
+  TcOperand ob{db, 2, OZ_B_PLANES * slices, (long long)Nt * kp, Nt, kp, g.K, 1, kp};
   CUtensorMap ma, mb;
-  e = tc_make_map(&ma, oa, OZ_TM, 2);
-  if (!e) e = tc_make_map(&mb, ob, OZ_TN, 2);
+  e = tc_make_map(&ma, oa, OZ_TM, OZ_A_PLANES);
+  if (!e) e = tc_make_map(&mb, ob, OZ_TN, OZ_B_PLANES);
   if (e) return e;
   OzArgs a;
   std::memset(&a, 0, sizeof(a));
