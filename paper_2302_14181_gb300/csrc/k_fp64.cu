@@ -718,9 +718,12 @@ __device__ Refl apply_then_reflect(double2* col, const double2* v, double2 t, in
 
 // Cooperative Householder factorisation, one launch for all columns. CTA c owns
 // columns j = c, c + G, c + 2G, ... (G = grid size), kept in shared memory. At
-// step k the owner of column k publishes reflector k (V[k.., k], tau[k],
-// beta[k], then a release flag), every other CTA acquires it and applies H_k^H
-// to its own columns > k. The owner of column k + 1 updates that column first
+// step k the owner of column k publishes reflector k (V[k.., k], tau_k in
+// V[k - 1, k], tau[k], beta[k]), every other CTA acquires it and applies H_k^H
+// to its own columns > k. V starts filled with a value no entry can take, so a
+// consumer polls the entries it reads until they are written (no flag and
+// second round trip); reflector 0 alone, which has no row above it, is
+// published by a release flag. The owner of column k + 1 updates that column first
 // and publishes reflector k + 1 before updating its other columns, so the chain
 // of dependent work per step is one column update plus one norm; the rows of
 // V above the diagonal and the R part of the column, which only later kernels
@@ -743,6 +746,39 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// V is filled with this byte pattern (0x7F in every byte, about 1.38e306 as a
+// double) before the factorisation. No entry of a reflector (|v_r| <= 1, the
+// scale of a column by 1 / (alpha - beta) with |alpha - beta| >= |x|), of a tau
+// (|tau| <= 2) or of the zeros above can equal it, so an entry of V that no
+// longer holds it in both halves has its final value: a consumer polls the rows
+// it reads instead of a flag and then the rows.
+constexpr unsigned long long QR_V_UNSET = 0x7F7F7F7F7F7F7F7Full;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const void* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// the entry at p once both of its halves are written; false after the time
+// limit (err set to code)
+__device__ bool poll_entry(const double2* p, double2& out, int* err, int code) {
+  unsigned long long re = ld_relaxed_u64(&p->x), im = ld_relaxed_u64(&p->y);
+  if (re == QR_V_UNSET || im == QR_V_UNSET) {
+    const unsigned long long t0 = qr_gtimer();
+    while (re == QR_V_UNSET || im == QR_V_UNSET) {
+      if (qr_gtimer() - t0 > QR_WAIT_NS) {
+        atomicExch(err, code);
+        return false;
+      }
+      if (re == QR_V_UNSET) re = ld_relaxed_u64(&p->x);
+      if (im == QR_V_UNSET) im = ld_relaxed_u64(&p->y);
+    }
+  }
+  out = make_double2(__longlong_as_double((long long)re), __longlong_as_double((long long)im));
+  return true;
 }
 
 __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, double2* V, double2* tau,
@@ -778,9 +814,10 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
       if (k > 0) V[(long long)k * m + k - 1] = s_refl.tau;
     }
     // the block barrier orders every thread's stores of V before thread 0's
-    // release store, which is cumulative over them (one release per block)
+    // release store, which is cumulative over them (reflector 0 only: the
+    // consumers of the others poll V itself), and publishes s_tau to the block
     __syncthreads();
-    if (threadIdx.x == 0) st_release(flags + k, epoch);
+    if (threadIdx.x == 0 && k == 0) st_release(flags + k, epoch);
     // rows above k - 1: zeros of V, and the R part of column k for qr64_extract_r
     const double2* col = cols + (size_t)(k / G) * m;
     for (int r = threadIdx.x; r < k; r += blockDim.x) {
@@ -796,8 +833,23 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
   for (int k = 0; k < n; ++k) {
     const int owner = k % G;
     double2* v = vb[k & 1];
-    if (owner != c) {
-      // acquire reflector k
+    if (owner != c && k > 0) {
+      // reflector k: each thread polls the rows of V_k it reads first (its own
+      // rows of the dot products below), and the last thread tau_k in row
+      // k - 1; other threads read them only after a reduction's barrier
+      const double2* Vk = V + (long long)k * m;
+      bool ok = true;
+      for (int r = k + threadIdx.x; r < m && ok; r += blockDim.x) ok = poll_entry(Vk + r, v[r], err, 8);
+      if (ok && threadIdx.x == blockDim.x - 1) {
+        double2 t;
+        ok = poll_entry(Vk + k - 1, t, err, 8);
+        s_tau[k & 1] = t;
+      }
+      if (!ok) s_abort = 1;
+      __syncthreads();
+      if (s_abort) return;
+    } else if (owner != c) {
+      // reflector 0 (no row above it for tau): acquire its flag
       if (threadIdx.x == 0) {
         if (ld_acquire(flags + k) != epoch) {
           const unsigned long long t0 = qr_gtimer();
@@ -812,13 +864,9 @@ __global__ void __launch_bounds__(256) qr_coop_kernel(double2* A, int m, int n, 
       }
       __syncthreads();
       if (s_abort) return;
-      // each thread loads the rows it reads first (its own rows of the dot
-      // products below); other threads read them only after a reduction's
-      // barrier. tau_k comes from row k - 1 of the column (tau[0] for k = 0),
-      // in the same round of loads.
       const double2* Vk = V + (long long)k * m;
       for (int r = k + threadIdx.x; r < m; r += blockDim.x) v[r] = __ldcg(Vk + r);  // L2, never a stale L1 line
-      if (threadIdx.x == blockDim.x - 1) s_tau[k & 1] = k > 0 ? __ldcg(Vk + k - 1) : __ldcg(tau);
+      if (threadIdx.x == blockDim.x - 1) s_tau[k & 1] = __ldcg(tau);
       __syncthreads();
     }
     const double2 t = s_tau[k & 1];
@@ -1059,6 +1107,8 @@ int qr64_factor_coop(const Launch& L, z64* A_, int m, int n, z64* V_, z64* tau_,
   double2* V = reinterpret_cast<double2*>(V_);
   double2* tau = reinterpret_cast<double2*>(tau_);
   double2* beta = reinterpret_cast<double2*>(beta_);
+  // every entry of V starts as QR_V_UNSET (the kernel writes all of them)
+  if (cudaMemsetAsync(V, 0x7F, sizeof(double2) * (size_t)m * n, L.stream) != cudaSuccess) return TEVO_ECUDA;
   void* args[] = {&A, &m, &n, &V, &tau, &beta, &frob2, &flags, &epoch, &err};
   cudaError_t e = cudaLaunchCooperativeKernel((void*)qr_coop_kernel, dim3(G), dim3(256), args, smem, L.stream);
   ++*L.launches;

@@ -32,7 +32,7 @@
 //
 // The tensor-core schedule is that of the plain complex GEMM (k_tc.cu): a
 // persistent CTA per SM, a TMA producer warp, one thread issuing tcgen05.mma,
-// eight epilogue warps (two per tensor-memory lane quarter), two tensor-memory
+// twelve epilogue warps (three per tensor-memory lane quarter), two tensor-memory
 // accumulator buffers (a pass drains while the next accumulates). A stage holds
 // the (re, im) planes of one A slice and the (-im, re, im) planes of one B slice
 // for 32 K-indices. The accumulator of a 128 x 128 complex tile is one
@@ -77,12 +77,14 @@ constexpr int OZ_B_BYTES = OZ_B_PLANES * OZ_TN * OZ_KCB;  // 24 KB
 constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
 constexpr int OZ_SMEM_BYTES = OZ_NSTAGE * OZ_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 #ifndef OZ_EPILOGUE_WARPS
-#define OZ_EPILOGUE_WARPS 8
+#define OZ_EPILOGUE_WARPS 12
 #endif
-// epilogue warps: one or two per tensor-memory lane quarter (4 or 8), each on
-// all or half of the tile's columns
+// epilogue warps: one to four per tensor-memory lane quarter, each on a run of
+// the tile's columns. Twelve (three per quarter, 128 registers a thread) keep
+// 1.5x the fixed-point-sum loads of eight in flight and ran the kernel 2-9 %
+// faster; sixteen spill at the 96 registers a thread they leave.
 constexpr int OZ_EPI_WARPS = OZ_EPILOGUE_WARPS;
-static_assert(OZ_EPI_WARPS == 4 || OZ_EPI_WARPS == 8, "epilogue warps");
+static_assert(OZ_EPI_WARPS % 4 == 0 && OZ_EPI_WARPS <= 16, "epilogue warps");
 constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
 // one operand to cut into digit slices: element (r, k) of R x K at
 // src[(r / R2) * sR1 + (r % R2) * sR + k * sK] (conjugated when conj), digit
@@ -339,6 +341,43 @@ __device__ __forceinline__ int digit_of(unsigned long long U, int s, int G) {
   return d < -(1 << OZ_P) ? -(1 << OZ_P) : d;
 }
 
+// the digit planes of two neighbouring entries v0, v1 = (r, k), (r, k + 1) of a
+// row with exponent e (OZ_NONFINITE: zeros), written as one 4-byte bf16 pair
+// per plane; digit_bf16 holds the bf16 of the integers -2^P .. 2^P
+__device__ __forceinline__ void write_digit_pair(const OzSplit& o, long long r, int k, int e, double2 v0, double2 v1,
+                                                 const __nv_bfloat16* digit_bf16) {
+  const int F = OZ_P + OZ_W * (o.G - 1);
+  const bool fin = e != OZ_NONFINITE;
+  unsigned long long C = 0;
+  for (int s = 0; s < o.G; ++s) C += (1ull << OZ_P) << (OZ_W * (o.G - 1 - s));
+  const unsigned long long u0r = (unsigned long long)(fin ? to_fixed(v0.x, e, F) : 0) + C;
+  const unsigned long long u0i = (unsigned long long)(fin ? to_fixed(v0.y, e, F) : 0) + C;
+  const unsigned long long u1r = (unsigned long long)(fin ? to_fixed(v1.x, e, F) : 0) + C;
+  const unsigned long long u1i = (unsigned long long)(fin ? to_fixed(v1.y, e, F) : 0) + C;
+  __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(o.dst + r * o.row_pitch + k);
+  const long long ps2 = o.plane_stride / 2;  // plane stride in bf16 pairs (even: rows are padded to 8)
+  constexpr int H = 1 << OZ_P;
+  for (int s = 0; s < o.G; ++s) {
+    __nv_bfloat162 re, im;
+    re.x = digit_bf16[digit_of(u0r, s, o.G) + H];
+    re.y = digit_bf16[digit_of(u1r, s, o.G) + H];
+    const int d0i = digit_of(u0i, s, o.G), d1i = digit_of(u1i, s, o.G);
+    im.x = digit_bf16[d0i + H];
+    im.y = digit_bf16[d1i + H];
+    if (o.planes == 3) {
+      __nv_bfloat162 nim;
+      nim.x = digit_bf16[H - d0i];
+      nim.y = digit_bf16[H - d1i];
+      dst[(long long)(3 * s) * ps2] = nim;
+      dst[(long long)(3 * s + 1) * ps2] = re;
+      dst[(long long)(3 * s + 2) * ps2] = im;
+    } else {
+      dst[(long long)(2 * s) * ps2] = re;
+      dst[(long long)(2 * s + 1) * ps2] = im;
+    }
+  }
+}
+
 // digit planes [planes G][R][row_pitch] (planes = 2: plane 2s = Re of slice s,
 // 2s+1 = Im; planes = 3: 3s = -Im, 3s+1 = Re, 3s+2 = Im) of a 32-row x 64-K tile, staged in shared memory so that the fp64 reads (along the
 // contiguous source index) are coalesced; each thread then forms the digits of
@@ -369,44 +408,67 @@ __global__ void oz_slice_kernel(OzSplit o) {
       }
   }
   __syncthreads();
-  const int F = OZ_P + OZ_W * (o.G - 1);
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int r = r0 + i, k = k0 + 2 * threadIdx.x;
     if (r >= o.R || k >= o.K) continue;
     const int er = o.rowexp[r];
     const int e = er == OZ_NONE ? 0 : er;  // a zero row
     if (k0 == 0 && threadIdx.x == 0) o.exps[r] = e;
-    const bool fin = e != OZ_NONFINITE;
     // entries past K are zero (tile padding), so the pair never needs a tail case
-    const double2 v0 = tile[i][2 * threadIdx.x], v1 = tile[i][2 * threadIdx.x + 1];
-    unsigned long long C = 0;
-    for (int s = 0; s < o.G; ++s) C += (1ull << OZ_P) << (OZ_W * (o.G - 1 - s));
-    const unsigned long long u0r = (unsigned long long)(fin ? to_fixed(v0.x, e, F) : 0) + C;
-    const unsigned long long u0i = (unsigned long long)(fin ? to_fixed(v0.y, e, F) : 0) + C;
-    const unsigned long long u1r = (unsigned long long)(fin ? to_fixed(v1.x, e, F) : 0) + C;
-    const unsigned long long u1i = (unsigned long long)(fin ? to_fixed(v1.y, e, F) : 0) + C;
-    __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(o.dst + (long long)r * o.row_pitch + k);
-    const long long ps2 = o.plane_stride / 2;  // plane stride in bf16 pairs (even: rows are padded to 8)
-    constexpr int H = 1 << OZ_P;
-    for (int s = 0; s < o.G; ++s) {
-      __nv_bfloat162 re, im;
-      re.x = digit_bf16[digit_of(u0r, s, o.G) + H];
-      re.y = digit_bf16[digit_of(u1r, s, o.G) + H];
-      const int d0i = digit_of(u0i, s, o.G), d1i = digit_of(u1i, s, o.G);
-      im.x = digit_bf16[d0i + H];
-      im.y = digit_bf16[d1i + H];
-      if (o.planes == 3) {
-        __nv_bfloat162 nim;
-        nim.x = digit_bf16[H - d0i];
-        nim.y = digit_bf16[H - d1i];
-        dst[(long long)(3 * s) * ps2] = nim;
-        dst[(long long)(3 * s + 1) * ps2] = re;
-        dst[(long long)(3 * s + 2) * ps2] = im;
-      } else {
-        dst[(long long)(2 * s) * ps2] = re;
-        dst[(long long)(2 * s + 1) * ps2] = im;
-      }
+    write_digit_pair(o, r, k, e, tile[i][2 * threadIdx.x], tile[i][2 * threadIdx.x + 1], digit_bf16);
+  }
+}
+
+// rows of at most OZ_FUSED_MAX_K entries: a block holds OZ_FUSED_ROWS(K) whole
+// rows in shared memory, takes each row's exponent (a warp per row) and writes
+// its digit planes, so the operand is read once and no exponent pass runs.
+// The exponent and the digits are those of oz_rowmax_* and oz_slice_kernel.
+constexpr int OZ_FUSED_MAX_K = 512;
+__host__ __device__ constexpr int oz_fused_rows(int K) { return K <= 128 ? 32 : K <= 256 ? 16 : 8; }
+// shared memory of a block for K (rows of 64-padded K plus one, to spread the banks)
+__host__ __device__ constexpr int oz_fused_smem(int K) { return oz_fused_rows(K) * ((K + 63) / 64 * 64 + 1) * 16; }
+constexpr int OZ_FUSED_SMEM = 32 * 129 * 16;  // the largest of oz_fused_smem (K = 128): 64.5 KB
+static_assert(oz_fused_smem(128) == OZ_FUSED_SMEM && oz_fused_smem(256) <= OZ_FUSED_SMEM &&
+                  oz_fused_smem(512) <= OZ_FUSED_SMEM && oz_fused_smem(64) <= OZ_FUSED_SMEM,
+              "fused slicing shared memory");
+
+template <bool ROWS_CONTIG>
+__global__ void __launch_bounds__(256) oz_slice_rows_kernel(OzSplit o) {
+  extern __shared__ double2 rows[];  // [RB][Kc + 1]
+  __shared__ __nv_bfloat16 digit_bf16[2 * (1 << OZ_P) + 1];
+  __shared__ int s_e[32];
+  const int RB = oz_fused_rows(o.K), Kc = (o.K + 63) / 64 * 64, ld = Kc + 1;
+  const long long r0 = (long long)blockIdx.x * RB;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int t = tid; t <= 2 * (1 << OZ_P); t += 256) digit_bf16[t] = __float2bfloat16_rn((float)(t - (1 << OZ_P)));
+  // consecutive threads read consecutive addresses: rows when rows are
+  // contiguous, K otherwise
+  for (int idx = tid; idx < RB * Kc; idx += 256) {
+    const int i = ROWS_CONTIG ? idx % RB : idx / Kc, k = ROWS_CONTIG ? idx / RB : idx % Kc;
+    const long long r = r0 + i;
+    double2 v = make_double2(0.0, 0.0);
+    if (r < o.R && k < o.K) v = o.src[row_offset(o, r) + (long long)k * o.sK];
+    if (o.conj) v.y = -v.y;
+    rows[i * ld + k] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < RB; i += 8) {
+    int mx = OZ_NONE;
+    for (int k = threadIdx.x; k < o.K; k += 32) mx = max(mx, exp_bound(rows[i * ld + k]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (threadIdx.x == 0) {
+      const int e = mx == OZ_NONE ? 0 : mx;  // a zero row
+      s_e[i] = e;
+      if (r0 + i < o.R) o.exps[r0 + i] = e;
     }
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < RB; i += 8) {
+    const long long r = r0 + i;
+    if (r >= o.R) continue;
+    for (int k = 2 * threadIdx.x; k < o.K; k += 64)
+      write_digit_pair(o, r, k, s_e[i], rows[i * ld + k], rows[i * ld + k + 1], digit_bf16);
   }
 }
 
@@ -568,16 +630,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
     }
   } else {
-    // epilogue: warps 2..9; warp w owns tensor-memory lane quarter w % 4 and half
-    // of the tile's columns. A pass value is an exact integer held in fp32; the
+    // epilogue: warps 2..; warp w owns tensor-memory lane quarter w % 4 and a
+    // run of the tile's columns. A pass value is an exact integer held in fp32; the
     // passes of a unit are summed with integer operations only, groups 0..3 in
     // the 64-bit fixed-point accumulator S0 and groups 4..7 in S1 (unit 2^-28 of
     // S0's), both exact. They live in this CTA's slice of the workspace, laid
     // out [column][row] so that a warp touches 32 consecutive rows, and the entry
     // is converted to fp64 once, after the unit's last pass.
     const int qw = warp % 4;
-    const int c_lo = ((warp - 2) / 4) * (OZ_TN * 4 / OZ_EPI_WARPS);  // this warp's columns
-    const int c_hi = c_lo + OZ_TN * 4 / OZ_EPI_WARPS;
+    // this warp's columns: the tile's 128 split over the warps of a lane quarter
+    // in runs of 16 (twelve warps: 48, 48, 32)
+    const int nq = OZ_EPI_WARPS / 4, run = (warp - 2) / 4;
+    const int per = ((OZ_TN / 16 + nq - 1) / nq) * 16;
+    const int c_lo = min(OZ_TN, run * per);
+    const int c_hi = min(OZ_TN, c_lo + per);
     const int row = qw * 32 + lane;
     longlong2* S0 = a.acc + (size_t)blockIdx.x * 2 * OZ_TM * OZ_TN + row;
     longlong2* S1 = S0 + OZ_TM * OZ_TN;
@@ -703,8 +769,23 @@ OzPlan plan(int M, int N, int K, int G, int num_sms) {
 }
 
 int split_operand(const Launch& L, const OzSplit& o) {
-  if (cudaMemsetAsync(o.rowexp, 0x80, sizeof(int) * (size_t)o.R, L.stream) != cudaSuccess) return TEVO_ECUDA;
   const bool rows_contig = o.sR == 1 && o.sK != 1;
+  if (o.K <= OZ_FUSED_MAX_K) {
+    static std::atomic<unsigned long long> attr_t{0}, attr_f{0};
+    if (smem_attr_once(oz_slice_rows_kernel<true>, OZ_FUSED_SMEM, attr_t) ||
+        smem_attr_once(oz_slice_rows_kernel<false>, OZ_FUSED_SMEM, attr_f))
+      return TEVO_ECUDA;
+    const long long nb = ((long long)o.R + oz_fused_rows(o.K) - 1) / oz_fused_rows(o.K);
+    if (nb > (1LL << 31) - 1) return TEVO_ESHAPE;
+    const dim3 block(32, 8);
+    if (rows_contig)
+      oz_slice_rows_kernel<true><<<(unsigned)nb, block, oz_fused_smem(o.K), L.stream>>>(o);
+    else
+      oz_slice_rows_kernel<false><<<(unsigned)nb, block, oz_fused_smem(o.K), L.stream>>>(o);
+    ++*L.launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+  }
+  if (cudaMemsetAsync(o.rowexp, 0x80, sizeof(int) * (size_t)o.R, L.stream) != cudaSuccess) return TEVO_ECUDA;
   if (rows_contig) {
     const int nseg = (o.K + 63) / 64;
     oz_rowmax_lane_kernel<<<grid_of(((long long)o.R + 31) / 32 * nseg * 32, 256, L.num_sms), 256, 0, L.stream>>>(o, nseg);
