@@ -1229,8 +1229,15 @@ extern "C" int measure_local(tevo_mps s, int nops, const double* ops, double* ou
   }
   size_t bq = 0;
   for (int i = 0; i < L; ++i) bq = std::max(bq, (size_t)s->dims[i] * d * s->dims[i + 1]);
-  Buf El, Er, Y, Z, Wm, OA, opsd, vals;
+  // a state left by evolve_step is right-canonical from site 1 on (its sites
+  // are the isometries of the last leftward sweep): its right transfer
+  // matrices are identities, and <O_i> needs only the site's density
+  // rho_i[s][t] = sum conj(A_i[a0][s][a]) (El_i A_i)[a0][t][a] from the left
+  // sweep (no per-operator contractions)
+  const bool dens = s->canonical && d <= 4;
+  Buf El, Er, Y, Z, Wm, OA, opsd, vals, part;
   int e = dalloc(c, El, sizeof(z64) * tot);
+  if (!e && dens) e = dalloc(c, part, sizeof(z64) * rho_part_count(L, d));
   if (!e) e = dalloc(c, Er, sizeof(z64) * tot);
   if (!e) e = dalloc(c, Y, sizeof(z64) * bq);
   if (!e) e = dalloc(c, Z, sizeof(z64) * bq);
@@ -1242,7 +1249,7 @@ extern "C" int measure_local(tevo_mps s, int nops, const double* ops, double* ou
   if (!e) e = ensure(c, s->red, sizeof(double) * 4096);
   if (!e) e = ensure(c, s->Atmp, sizeof(z64) * bq);
   auto cleanup = [&]() {
-    for (Buf* b : {&El, &Er, &Y, &Z, &Wm, &OA, &opsd, &vals}) dfree(c, *b);
+    for (Buf* b : {&El, &Er, &Y, &Z, &Wm, &OA, &opsd, &vals, &part}) dfree(c, *b);
   };
   auto run = [&]() -> int {
     TRYCUDA(cudaMemcpyAsync(opsd.p, ops, sizeof(z64) * (size_t)nops * d * d, cudaMemcpyHostToDevice, c->stream));
@@ -1255,12 +1262,11 @@ extern "C" int measure_local(tevo_mps s, int nops, const double* ops, double* ou
       const int Dl = s->dims[i], Dr = s->dims[i + 1];
       TRY(gemm(s, gd(el + off[i], 0, Dl, 1, s->A[i].p, 0, (long long)d * Dr, 1, Y.p, 0, (long long)d * Dr, 1, Dl,
                      d * Dr, Dl, 1)));
+      if (dens) TRY(rho_partial64(Lc, zp(s->A[i]), zp(Y), Dl, d, Dr, zp(part) + rho_part_count(i, d)));
       TRY(gemm(s, gd(s->A[i].p, 0, 1, Dr, Y.p, 0, Dr, 1, el + off[i + 1], 0, Dr, 1, Dr, Dr, Dl * d, 1, 1)));
     }
-    // a state left by evolve_step is right-canonical from site 1 on (its sites
-    // are the isometries of the last leftward sweep): its right transfer
-    // matrices are identities
-    if (s->canonical) {
+    if (dens) TRY(rho_apply64(Lc, zp(part), L, d, zp(opsd), nops, zp(vals)));
+    if (s->canonical && !dens) {
       for (int i = 1; i < L; ++i) TRY(eye64(Lc, er + off[i], s->dims[i]));
     }
     for (int i = L - 1; i >= 0 && !s->canonical; --i) {
@@ -1270,7 +1276,7 @@ extern "C" int measure_local(tevo_mps s, int nops, const double* ops, double* ou
                      Dr, d * Dl, Dr, 1)));
       TRY(gemm(s, gd(s->Atmp.p, 0, 1, Dl, Y.p, 0, Dl, 1, er + off[i], 0, Dl, 1, Dl, Dl, Dr * d, 1, 1)));
     }
-    for (int i = 0; i < L; ++i) {
+    for (int i = 0; i < L && !dens; ++i) {
       const int Dl = s->dims[i], Dr = s->dims[i + 1];
       for (int k = 0; k < nops; ++k) {
         // OA[a][s][b] = sum_t O[s][t] A[a][t][b]   (batched over a)

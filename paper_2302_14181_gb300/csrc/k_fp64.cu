@@ -1273,6 +1273,60 @@ __global__ void dotu_final_kernel(const double* part, int np, double2* out) {
   if (threadIdx.x == 0) *out = t;
 }
 
+// one site's density in the mixed gauge with identity right transfers:
+// part[blk][s][t] = sum over this block's (a0, a) of conj(A[a0][s][a]) Y[a0][t][a]
+// for A, Y of shape [Dl][d][Dr] (Y = El A), d <= RHO_MAX_D; each of the d^2
+// sums in block_csum's fixed order
+constexpr int RHO_MAX_D = 4;
+constexpr int RHO_BLOCKS = 64;
+__global__ void rho_partial_kernel(const double2* A, const double2* Y, int Dl, int d, int Dr, double2* part) {
+  __shared__ double red[64];
+  double2 acc[RHO_MAX_D * RHO_MAX_D];
+#pragma unroll
+  for (int j = 0; j < RHO_MAX_D * RHO_MAX_D; ++j) acc[j] = make_double2(0.0, 0.0);
+  const long long n = (long long)Dl * Dr;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long a0 = idx / Dr, a = idx % Dr;
+    const double2* Ar = A + a0 * d * Dr + a;
+    const double2* Yr = Y + a0 * d * Dr + a;
+#pragma unroll
+    for (int s = 0; s < RHO_MAX_D; ++s)
+#pragma unroll
+      for (int t = 0; t < RHO_MAX_D; ++t)
+        if (s < d && t < d) acc[s * RHO_MAX_D + t] = cfma(cconj(Ar[(long long)s * Dr]), Yr[(long long)t * Dr],
+                                                          acc[s * RHO_MAX_D + t]);
+  }
+#pragma unroll
+  for (int s = 0; s < RHO_MAX_D; ++s)
+#pragma unroll
+    for (int t = 0; t < RHO_MAX_D; ++t)
+      if (s < d && t < d) {  // uniform across the block
+        const double2 v = block_csum(acc[s * RHO_MAX_D + t], red);
+        if (threadIdx.x == 0) part[(long long)blockIdx.x * d * d + s * d + t] = v;
+      }
+}
+
+// vals[k][i] = sum_{s,t} O_k[s][t] rho_i[s][t], rho_i the blocks' partials of
+// site i summed in block order (one thread per (k, i))
+__global__ void rho_apply_kernel(const double2* part, int L, int d, const double2* ops, int nops, double2* vals) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nops * L) return;
+  const int k = idx / L, i = idx % L;
+  double2 v = make_double2(0.0, 0.0);
+  for (int s = 0; s < d; ++s)
+    for (int t = 0; t < d; ++t) {
+      double2 r = make_double2(0.0, 0.0);
+      for (int b = 0; b < RHO_BLOCKS; ++b) {
+        const double2 p = part[((long long)i * RHO_BLOCKS + b) * d * d + s * d + t];
+        r.x += p.x;
+        r.y += p.y;
+      }
+      v = cfma(ops[(long long)k * d * d + s * d + t], r, v);
+    }
+  vals[idx] = v;
+}
+
 __global__ void rescale_kernel(double2* E, long long n, const double* nrm2, double* logacc) {
   const double s2 = *nrm2;
   if (!(s2 > 0.0) || !isfinite(s2)) return;
@@ -1349,6 +1403,26 @@ int dotu64(const Launch& L, const z64* a, const z64* b, size_t n, z64* out, doub
                                                          reinterpret_cast<const double2*>(b), (long long)n, scratch);
   dotu_final_kernel<<<1, 256, 0, L.stream>>>(scratch, FROB_BLOCKS, reinterpret_cast<double2*>(out));
   *L.launches += 2;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+size_t rho_part_count(int L, int d) { return (size_t)L * RHO_BLOCKS * d * d; }
+
+int rho_partial64(const Launch& L, const z64* A, const z64* Y, int Dl, int d, int Dr, z64* part) {
+  if (d < 1 || d > RHO_MAX_D) return TEVO_EUNSUPPORTED;
+  rho_partial_kernel<<<RHO_BLOCKS, 256, 0, L.stream>>>(reinterpret_cast<const double2*>(A),
+                                                      reinterpret_cast<const double2*>(Y), Dl, d, Dr,
+                                                      reinterpret_cast<double2*>(part));
+  ++*L.launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
+}
+
+int rho_apply64(const Launch& L, const z64* part, int nsites, int d, const z64* ops, int nops, z64* vals) {
+  const int n = nops * nsites;
+  rho_apply_kernel<<<(n + 127) / 128, 128, 0, L.stream>>>(reinterpret_cast<const double2*>(part), nsites, d,
+                                                          reinterpret_cast<const double2*>(ops), nops,
+                                                          reinterpret_cast<double2*>(vals));
+  ++*L.launches;
   return cudaGetLastError() == cudaSuccess ? 0 : TEVO_ECUDA;
 }
 

@@ -151,6 +151,14 @@ int norm2_64(const Launch& L, const z64* x, size_t n, double* out, double* scrat
 int normalize64(const Launch& L, z64* x, size_t n, const double* nrm2, double* lognorm, int* flag);
 // sum_i a[i] * b[i] (no conjugation) into *out (device, complex)
 int dotu64(const Launch& L, const z64* a, const z64* b, size_t n, z64* out, double* scratch);
+// site densities for local observables of a state whose right transfers are
+// identities: rho_partial64 writes site i's block partials of
+// rho[s][t] = sum conj(A[a0][s][a]) Y[a0][t][a] (Y = El A, both [Dl][d][Dr],
+// d <= 4) to part (rho_part_count(1, d) entries per site), rho_apply64 sums each
+// site's partials in a fixed order and writes vals[k][i] = sum_{s,t} O_k[s][t] rho_i[s][t]
+size_t rho_part_count(int L, int d);
+int rho_partial64(const Launch& L, const z64* A, const z64* Y, int Dl, int d, int Dr, z64* part);
+int rho_apply64(const Launch& L, const z64* part, int nsites, int d, const z64* ops, int nops, z64* vals);
 // E /= ||E||_F, *logacc += log ||E||_F (overlap transfer rescaling)
 int rescale64(const Launch& L, z64* E, size_t n, double* logacc, double* scratch);
 
