@@ -304,8 +304,16 @@ __global__ void oz_rowmax_warp_kernel(OzSplit o, int nseg) {
     const long long r = w / nseg;
     const int k0 = int(w % nseg) * 256;
     const double2* src = o.src + row_offset(o, r);
+    // the segment's eight loads per lane issued together
+    double2 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = k0 + lane + 32 * j;
+      v[j] = k < o.K ? src[(long long)k * o.sK] : make_double2(0.0, 0.0);
+    }
     int mx = OZ_NONE;
-    for (int k = k0 + lane; k < min(o.K, k0 + 256); k += 32) mx = max(mx, exp_bound(src[(long long)k * o.sK]));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) mx = max(mx, exp_bound(v[j]));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     if (lane == 0 && mx != OZ_NONE) atomicMax(o.rowexp + r, mx);
@@ -424,12 +432,13 @@ __global__ void oz_slice_kernel(OzSplit o) {
 // its digit planes, so the operand is read once and no exponent pass runs.
 // The exponent and the digits are those of oz_rowmax_* and oz_slice_kernel.
 constexpr int OZ_FUSED_MAX_K = 512;
-__host__ __device__ constexpr int oz_fused_rows(int K) { return K <= 128 ? 32 : K <= 256 ? 16 : 8; }
+// rows per block: about 32 KB of shared memory, so that several blocks share an SM
+__host__ __device__ constexpr int oz_fused_rows(int K) { return K <= 64 ? 32 : K <= 128 ? 16 : K <= 256 ? 8 : 4; }
 // shared memory of a block for K (rows of 64-padded K plus one, to spread the banks)
 __host__ __device__ constexpr int oz_fused_smem(int K) { return oz_fused_rows(K) * ((K + 63) / 64 * 64 + 1) * 16; }
-constexpr int OZ_FUSED_SMEM = 32 * 129 * 16;  // the largest of oz_fused_smem (K = 128): 64.5 KB
-static_assert(oz_fused_smem(128) == OZ_FUSED_SMEM && oz_fused_smem(256) <= OZ_FUSED_SMEM &&
-                  oz_fused_smem(512) <= OZ_FUSED_SMEM && oz_fused_smem(64) <= OZ_FUSED_SMEM,
+constexpr int OZ_FUSED_SMEM = 32 * 65 * 16;  // the largest of oz_fused_smem (K = 64): 32.5 KB
+static_assert(oz_fused_smem(64) == OZ_FUSED_SMEM && oz_fused_smem(128) <= OZ_FUSED_SMEM &&
+                  oz_fused_smem(256) <= OZ_FUSED_SMEM && oz_fused_smem(512) <= OZ_FUSED_SMEM,
               "fused slicing shared memory");
 
 template <bool ROWS_CONTIG>
@@ -442,14 +451,26 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(OzSplit o) {
   const int tid = threadIdx.y * 32 + threadIdx.x;
   for (int t = tid; t <= 2 * (1 << OZ_P); t += 256) digit_bf16[t] = __float2bfloat16_rn((float)(t - (1 << OZ_P)));
   // consecutive threads read consecutive addresses: rows when rows are
-  // contiguous, K otherwise
-  for (int idx = tid; idx < RB * Kc; idx += 256) {
-    const int i = ROWS_CONTIG ? idx % RB : idx / Kc, k = ROWS_CONTIG ? idx / RB : idx % Kc;
-    const long long r = r0 + i;
-    double2 v = make_double2(0.0, 0.0);
-    if (r < o.R && k < o.K) v = o.src[row_offset(o, r) + (long long)k * o.sK];
-    if (o.conj) v.y = -v.y;
-    rows[i * ld + k] = v;
+  // contiguous, K otherwise; up to eight loads in flight per thread before
+  // their shared-memory stores
+  const int ntile = RB * Kc;
+  for (int base = 0; base < ntile; base += 8 * 256) {
+    double2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * 256 + tid;
+      const int i = ROWS_CONTIG ? idx % RB : idx / Kc, k = ROWS_CONTIG ? idx / RB : idx % Kc;
+      const long long r = r0 + i;
+      v[u] = make_double2(0.0, 0.0);
+      if (idx < ntile && r < o.R && k < o.K) v[u] = o.src[row_offset(o, r) + (long long)k * o.sK];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * 256 + tid;
+      const int i = ROWS_CONTIG ? idx % RB : idx / Kc, k = ROWS_CONTIG ? idx / RB : idx % Kc;
+      if (o.conj) v[u].y = -v[u].y;
+      if (idx < ntile) rows[i * ld + k] = v[u];
+    }
   }
   __syncthreads();
   for (int i = threadIdx.y; i < RB; i += 8) {
@@ -464,10 +485,12 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(OzSplit o) {
     }
   }
   __syncthreads();
-  for (int i = threadIdx.y; i < RB; i += 8) {
+  // digits: with fewer than eight rows, the warps of a row split its K
+  const int wpr = RB >= 8 ? 1 : 8 / RB;
+  for (int i = threadIdx.y / wpr; i < RB; i += 8 / wpr) {
     const long long r = r0 + i;
     if (r >= o.R) continue;
-    for (int k = 2 * threadIdx.x; k < o.K; k += 64)
+    for (int k = 2 * threadIdx.x + 64 * (threadIdx.y % wpr); k < o.K; k += 64 * wpr)
       write_digit_pair(o, r, k, s_e[i], rows[i * ld + k], rows[i * ld + k + 1], digit_bf16);
   }
 }
