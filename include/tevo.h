@@ -181,8 +181,9 @@ int mps_destroy(tevo_mps psi);
  * a rebuild of the right environments) is fp64 (with sweeps = 1 the step is all
  * fp64); OR-ing TEVO_TC_ONLY makes every sweep a tensor-core sweep, OR-ing
  * TEVO_OZAKI computes the fp64 contractions with the tensor-core Ozaki scheme
- * (TEVO_OZAKI with TEVO_TC_ONLY is TEVO_EINVAL). The QR, the norm and every
- * reduction are fp64 in all forms.
+ * (TEVO_OZAKI with TEVO_TC_ONLY is TEVO_EINVAL); OR-ing TEVO_TWO_SITE (with
+ * TEVO_FP64, optionally TEVO_OZAKI) fits pairs of neighbouring sites instead of
+ * single sites. The QR, the norm and every reduction are fp64 in all forms.
  * Errors: TEVO_EINVAL, TEVO_ESHAPE, TEVO_ETAU, TEVO_ENOMEM, TEVO_ECUDA,
  * TEVO_ENONFINITE (norm of the fitted state is 0, NaN or Inf), TEVO_ETIMEOUT
  * (a bounded device wait gave up), TEVO_EUNSUPPORTED. The work is issued on
@@ -210,6 +211,11 @@ int evolve_step_batched(tevo_mps* psis, const tevo_mpo* Ws, int n, int sweeps, i
 /*
  * measure_local -- <O_i> = <psi|O_i|psi>/<psi|psi> for every site i and each of
  * nops single-site operators (the local observables of Sec. 8.2), in any gauge.
+ * The left transfer matrices are built site by site; for a state left by
+ * evolve_step (right-canonical from site 1 on, d <= 4) each value is
+ * sum_{s,t} O[s][t] rho_i[s][t] with the site density
+ * rho_i[s][t] = sum conj(A_i[a][s][b]) (El_i A_i)[a][t][b], otherwise the right
+ * transfer matrices are built as well and each operator is contracted in.
  * ops: complex [nops][d][d] host; out: complex [nops][L] host.
  * Errors: TEVO_EINVAL, TEVO_ENOMEM, TEVO_ECUDA. Synchronises the stream.
  */
